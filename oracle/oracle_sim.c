@@ -1,0 +1,227 @@
+/*
+ * oracle_sim.c -- plain serial CPU reference for cycle-based RTL stuck-at fault
+ * simulation. TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+ * CPU-baseline leg call it; the product path never does.
+ *
+ * What it computes is the plain definition of the problem (Sec. II-B, "RTL Fault
+ * Simulation"): inject ONE stuck-at fault, simulate the whole design cycle by cycle,
+ * and detect the fault by comparing the faulty values of the primary outputs with the
+ * good values obtained without faults. The paper's concurrent algorithm (good gate plus
+ * bad gates per node, Sec. II-B) simulates many faulty machines together; it must reach
+ * exactly this result, so the oracle is the one-machine-at-a-time definition written out,
+ * with no event skipping, no sharing between faults and no reordering:
+ *
+ *   good run:  Q[r] = 0;  for t in 0..T-1:
+ *                net[input i]  = stim[t][i] masked to its width
+ *                net[reg r]    = Q[r]
+ *                net[node n]   = op_n(operands) masked to width(n), in topological order
+ *                gout[t][o]    = net[outputs[o]]
+ *                Q[r]          = net[d_r] masked to width(r)     (global synchronization:
+ *                                the non-blocking-assignment latch at the end of the cycle)
+ *   fault (s, b, v): the same loop, but every time net[s] is produced (input read,
+ *                register read or node evaluation) it is forced: bit b := v
+ *                (the fault function applied at the injection node, Sec. IV-A, Table I).
+ *                At the end of the combinational settle of cycle t, before the latch, the
+ *                first output port o (lowest index) with net[outputs[o]] != gout[t][o]
+ *                detects the fault: result (1, t, o) and the machine stops (fault
+ *                dropping). After T cycles with no difference: (0, -1, -1).
+ *
+ * Readings where the paper is silent (it works on Verilog through iverilog):
+ *   2-valued logic (no X/Z); registers reset to 0; outputs sampled after the settle of
+ *   cycle t and before the latch (a register-driven output shows Q_t); cycle index
+ *   0-based; ties between ports go to the lowest port index; a stuck-at on a register
+ *   forces the Q its readers see, while the register still stores its D value.
+ *
+ * Op semantics: operands are zero-extended to 64 bits, the op is computed in uint64 and
+ * the result is masked to the node width. AND/OR/XOR bitwise; NOT ~a; ADD/SUB modulo
+ * 2^64 (hence 2^w after masking); MUX2 a!=0 ? b : c; EQ a==b, LT a<b (unsigned, 1-bit);
+ * SHL/SHR by the constant imm (imm >= 64 gives 0); SLICE a >> imm; CONCAT
+ * (a << width(b)) | b; CONST imm.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { O_AND, O_OR, O_XOR, O_NOT, O_ADD, O_SUB, O_MUX2, O_EQ, O_LT, O_SHL, O_SHR,
+       O_SLICE, O_CONCAT, O_CONST };
+
+typedef struct {
+    int32_t n_in, n_reg, n_node, n_out;
+    const uint8_t *in_w;       /* [n_in]   */
+    const uint8_t *reg_w;      /* [n_reg]  */
+    const uint32_t *reg_d;     /* [n_reg]  net latched by each register */
+    const uint8_t *op;         /* [n_node] */
+    const uint8_t *w;          /* [n_node] */
+    const uint32_t *a, *b, *c; /* [n_node] operand net ids */
+    const uint64_t *imm;       /* [n_node] */
+    const uint32_t *out;       /* [n_out]  net observed by each output port */
+} oracle_design;
+
+static uint64_t mask_of(unsigned w) { return w >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << w) - 1); }
+
+static unsigned net_width(const oracle_design *d, uint32_t net)
+{
+    if (net < (uint32_t)d->n_in) return d->in_w[net];
+    if (net < (uint32_t)(d->n_in + d->n_reg)) return d->reg_w[net - d->n_in];
+    return d->w[net - d->n_in - d->n_reg];
+}
+
+/* Topological order of the nodes by Kahn's algorithm over node->node operand edges.
+ * Returns 0, or -1 when the nodes form a combinational cycle. */
+int oracle_topo_order(const oracle_design *d, int32_t *order)
+{
+    int32_t N = d->n_node, base = d->n_in + d->n_reg;
+    int32_t *indeg = calloc((size_t)N + 1, sizeof(int32_t));
+    int32_t *cnt = calloc((size_t)N + 1, sizeof(int32_t));
+    int32_t *users = malloc(sizeof(int32_t) * (3 * (size_t)N + 1));
+    int32_t *queue = malloc(sizeof(int32_t) * ((size_t)N + 1));
+    int rc = 0;
+    /* operands of node i that are nodes themselves */
+    for (int32_t i = 0; i < N; i++) {
+        uint32_t ops[3] = {d->a[i], d->b[i], d->c[i]};
+        int nops = d->op[i] == O_CONST ? 0 : (d->op[i] == O_NOT || d->op[i] == O_SHL ||
+                   d->op[i] == O_SHR || d->op[i] == O_SLICE) ? 1 : d->op[i] == O_MUX2 ? 3 : 2;
+        for (int k = 0; k < nops; k++)
+            if (ops[k] >= (uint32_t)base) { indeg[i]++; cnt[ops[k] - base]++; }
+    }
+    /* CSR of users */
+    int32_t *start = calloc((size_t)N + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < N; i++) start[i + 1] = start[i] + cnt[i];
+    memset(cnt, 0, sizeof(int32_t) * ((size_t)N + 1));
+    for (int32_t i = 0; i < N; i++) {
+        uint32_t ops[3] = {d->a[i], d->b[i], d->c[i]};
+        int nops = d->op[i] == O_CONST ? 0 : (d->op[i] == O_NOT || d->op[i] == O_SHL ||
+                   d->op[i] == O_SHR || d->op[i] == O_SLICE) ? 1 : d->op[i] == O_MUX2 ? 3 : 2;
+        for (int k = 0; k < nops; k++)
+            if (ops[k] >= (uint32_t)base) {
+                int32_t p = ops[k] - base;
+                users[start[p] + cnt[p]++] = i;
+            }
+    }
+    int32_t head = 0, tail = 0, done = 0;
+    for (int32_t i = 0; i < N; i++) if (indeg[i] == 0) queue[tail++] = i;
+    while (head < tail) {
+        int32_t n = queue[head++];
+        order[done++] = n;
+        for (int32_t k = start[n]; k < start[n + 1]; k++)
+            if (--indeg[users[k]] == 0) queue[tail++] = users[k];
+    }
+    if (done != N) rc = -1;
+    free(indeg); free(cnt); free(users); free(queue); free(start);
+    return rc;
+}
+
+/* Evaluate node i from the current net values. */
+static uint64_t eval_node(const oracle_design *d, const uint64_t *net, int32_t i)
+{
+    uint64_t a = net[d->a[i]], b = 0, c = 0, r = 0, k = d->imm[i];
+    switch (d->op[i]) {
+    case O_AND:    b = net[d->b[i]]; r = a & b; break;
+    case O_OR:     b = net[d->b[i]]; r = a | b; break;
+    case O_XOR:    b = net[d->b[i]]; r = a ^ b; break;
+    case O_NOT:    r = ~a; break;
+    case O_ADD:    b = net[d->b[i]]; r = a + b; break;
+    case O_SUB:    b = net[d->b[i]]; r = a - b; break;
+    case O_MUX2:   b = net[d->b[i]]; c = net[d->c[i]]; r = (a != 0) ? b : c; break;
+    case O_EQ:     b = net[d->b[i]]; r = (a == b) ? 1 : 0; break;
+    case O_LT:     b = net[d->b[i]]; r = (a < b) ? 1 : 0; break;
+    case O_SHL:    r = k >= 64 ? 0 : (a << k); break;
+    case O_SHR:    r = k >= 64 ? 0 : (a >> k); break;
+    case O_SLICE:  r = k >= 64 ? 0 : (a >> k); break;
+    case O_CONCAT: {
+        unsigned wb = net_width(d, d->b[i]);
+        b = net[d->b[i]];
+        r = (wb >= 64 ? 0 : (a << wb)) | b;
+        break;
+    }
+    case O_CONST:  r = k; break;
+    default:       r = 0; break;
+    }
+    return r & mask_of(d->w[i]);
+}
+
+/* One machine over T cycles. With fault_net < 0 this is the good machine: it fills
+ * gout[T][n_out] and returns 0. Otherwise it compares against gout and returns the
+ * detection (cycle, port) through *cycle/*port (both -1 if never detected). */
+static void run_machine(const oracle_design *d, const int32_t *order, int32_t T,
+                        const uint64_t *stim, uint64_t *gout_w, const uint64_t *gout_r,
+                        uint64_t *trace_w,
+                        int64_t fault_net, unsigned fault_bit, unsigned fault_val,
+                        uint64_t *net, uint64_t *Q, int32_t *cycle, int32_t *port)
+{
+    int32_t I = d->n_in, R = d->n_reg, N = d->n_node, O = d->n_out;
+    uint64_t m1 = 0, m0 = 0;
+    if (fault_net >= 0) {
+        if (fault_val) m1 = (uint64_t)1 << fault_bit;
+        else           m0 = (uint64_t)1 << fault_bit;
+    }
+#define FORCE(netid) do { if ((int64_t)(netid) == fault_net) \
+                              net[netid] = (net[netid] & ~m0) | m1; } while (0)
+    for (int32_t r = 0; r < R; r++) Q[r] = 0;
+    *cycle = -1; *port = -1;
+    for (int32_t t = 0; t < T; t++) {
+        for (int32_t i = 0; i < I; i++) {
+            net[i] = stim[(size_t)t * I + i] & mask_of(d->in_w[i]);
+            FORCE(i);
+        }
+        for (int32_t r = 0; r < R; r++) {
+            net[I + r] = Q[r];
+            FORCE(I + r);
+        }
+        for (int32_t k = 0; k < N; k++) {
+            int32_t n = order[k];
+            net[I + R + n] = eval_node(d, net, n);
+            FORCE(I + R + n);
+        }
+        if (trace_w) memcpy(trace_w + (size_t)t * (I + R + N), net, sizeof(uint64_t) * (I + R + N));
+        if (fault_net < 0) {
+            for (int32_t o = 0; o < O; o++) gout_w[(size_t)t * O + o] = net[d->out[o]];
+        } else {
+            for (int32_t o = 0; o < O; o++) {
+                if (net[d->out[o]] != gout_r[(size_t)t * O + o]) {
+                    *cycle = t; *port = o;
+                    return;
+                }
+            }
+        }
+        for (int32_t r = 0; r < R; r++) Q[r] = net[d->reg_d[r]] & mask_of(d->reg_w[r]);
+    }
+#undef FORCE
+}
+
+static size_t n_nets(const oracle_design *d) { return (size_t)d->n_in + d->n_reg + d->n_node; }
+
+/* Good machine: gout[T][n_out] and, when trace is non-null, every net's value in every
+ * cycle, trace[T][n_in + n_reg + n_node]. Returns 0, or -1 on a combinational cycle. */
+int oracle_good_run(const oracle_design *d, int32_t T, const uint64_t *stim, uint64_t *gout,
+                    uint64_t *trace)
+{
+    int32_t *order = malloc(sizeof(int32_t) * ((size_t)d->n_node + 1));
+    if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
+    uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
+    uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
+    int32_t cy, po;
+    run_machine(d, order, T, stim, gout, NULL, trace, -1, 0, 0, net, Q, &cy, &po);
+    free(order); free(net); free(Q);
+    return 0;
+}
+
+/* Faulty machines, one after another, each compared against gout (from
+ * oracle_good_run). Writes detected/cycle/port per fault. Returns 0 or -1. */
+int oracle_fault_sim(const oracle_design *d, int32_t T, const uint64_t *stim,
+                     const uint64_t *gout, int32_t F, const uint32_t *fnet,
+                     const uint8_t *fbit, const uint8_t *fval,
+                     uint8_t *detected, int32_t *cycle, int32_t *port)
+{
+    int32_t *order = malloc(sizeof(int32_t) * ((size_t)d->n_node + 1));
+    if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
+    uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
+    uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
+    for (int32_t f = 0; f < F; f++) {
+        run_machine(d, order, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fval[f],
+                    net, Q, &cycle[f], &port[f]);
+        detected[f] = cycle[f] >= 0 ? 1 : 0;
+    }
+    free(order); free(net); free(Q);
+    return 0;
+}
