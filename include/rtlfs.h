@@ -1,0 +1,206 @@
+/*
+ * rtlfs.h -- C ABI of librtlfs, a GB300 (sm_103a) cycle-based RTL stuck-at fault
+ * simulator: the data-parallel hot path of RIROS (arXiv 2508.16376).
+ *
+ * Problem (Sec. II-B, "RTL Fault Simulation"): a design compiled into a graph of RTL
+ * nodes (variables and word-level operators) and registers is simulated cycle by cycle
+ * under a stimulus; registers take their next values at the end of every cycle (global
+ * synchronization, the non-blocking-assignment latch). A stuck-at-0/1 fault forces one
+ * bit of a wire, register or port (fault injection at the RTL node that produces the
+ * value, Sec. IV-A / Table I); the fault is detected when a faulty output value differs
+ * from the good one. The library returns, per fault, whether and when it is first
+ * detected and on which output port; a detected fault is dropped from further cycles.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status (RTLFS_OK or a negative RTLFS_E_* code); nothing
+ *    throws or aborts across the ABI. rtlfs_last_error() gives a one-line reason.
+ *  - Input arrays are host pointers, read during the call and copied (to device memory
+ *    where needed); the caller keeps ownership and may free them on return.
+ *  - Outputs are written into caller-allocated host buffers of the stated size.
+ *  - A failed call leaves the context's previous state unchanged, except RTLFS_E_CUDA,
+ *    after which the context should be destroyed.
+ *  - One context per host thread; a context owns all of its device memory and streams.
+ *  - Net id space of a design: [0, I) primary inputs, [I, I+R) register Q outputs,
+ *    [I+R, I+R+N) node outputs (node i drives net I+R+i). Values are unsigned words of
+ *    width 1..64 bits, held zero-extended in uint64; logic is 2-valued.
+ */
+#ifndef RTLFS_H
+#define RTLFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define RTLFS_OK          0
+#define RTLFS_E_ARG      -1   /* malformed argument: null pointer, id or size out of range */
+#define RTLFS_E_CYCLE    -2   /* the nodes form a combinational cycle */
+#define RTLFS_E_WIDTH    -3   /* a width is outside 1..64 or breaks an op's width rule */
+#define RTLFS_E_NOMEM    -4   /* device or host allocation failed */
+#define RTLFS_E_CUDA     -5   /* a CUDA call failed (destroy the context) */
+#define RTLFS_E_TIMEOUT  -6   /* a per-fault work budget ran out (results flagged) */
+#define RTLFS_E_STATE    -7   /* call out of order (e.g. run before stimulus/faults) */
+
+/* ---- word-level ops ------------------------------------------------------------------
+ * Operands are zero-extended to 64 bits, the op is computed in uint64 and the result is
+ * masked to the node width w. a, b, c are operand net ids; imm is a constant.
+ *   AND/OR/XOR  a op b            NOT   ~a
+ *   ADD/SUB     a +/- b mod 2^w   MUX2  a != 0 ? b : c
+ *   EQ/LT       a == b, a < b (unsigned); w must be 1
+ *   SHL/SHR     a << imm, a >> imm (imm >= 64 gives 0)
+ *   SLICE       a >> imm; requires imm + w <= width(a)
+ *   CONCAT      (a << width(b)) | b; requires w == width(a) + width(b) <= 64
+ *   CONST       imm (no operands)
+ * These stand for the RTL operator nodes of the paper's graph (Sec. II-B, Fig. 2); the
+ * paper's behavioral (VVP) nodes have no counterpart here. */
+enum rtlfs_op {
+    RTLFS_AND = 0, RTLFS_OR = 1, RTLFS_XOR = 2, RTLFS_NOT = 3, RTLFS_ADD = 4,
+    RTLFS_SUB = 5, RTLFS_MUX2 = 6, RTLFS_EQ = 7, RTLFS_LT = 8, RTLFS_SHL = 9,
+    RTLFS_SHR = 10, RTLFS_SLICE = 11, RTLFS_CONCAT = 12, RTLFS_CONST = 13
+};
+
+/* One operator node (24 bytes). Unused operand fields are ignored. */
+typedef struct {
+    uint8_t  op;        /* enum rtlfs_op */
+    uint8_t  width;     /* result width, 1..64 */
+    uint16_t reserved;  /* must be 0 */
+    uint32_t a, b, c;   /* operand net ids */
+    uint64_t imm;       /* shift amount, slice offset or constant */
+} rtlfs_node;
+
+/* One register (8 bytes): reset value 0; at the end of every cycle Q <- D masked to
+ * width (the global synchronization of Sec. II-B). d_net may be any net. */
+typedef struct {
+    uint32_t d_net;
+    uint8_t  width;     /* 1..64 */
+    uint8_t  reserved[3];
+} rtlfs_reg;
+
+/* One stuck-at fault (8 bytes): bit `bit` of net `net` forced to `stuck` (0 or 1) every
+ * time the net's value is produced -- input read, register read, node evaluation
+ * (unified fault injection at the producing node, Sec. IV-A). A register fault forces
+ * the Q its readers see; the register still stores its D value. */
+typedef struct {
+    uint32_t net;
+    uint8_t  bit;       /* < width(net) */
+    uint8_t  stuck;     /* 0 = stuck-at-0, 1 = stuck-at-1 */
+    uint16_t reserved;
+} rtlfs_fault;
+
+/* Per-fault result (12 bytes). Outputs are compared after the combinational settle of
+ * cycle `cycle` (0-based), before the latch; `port` is the lowest differing output
+ * index. Undetected: detected = 0, cycle = port = -1. detected = 255 marks a fault
+ * whose work budget ran out (the run returns RTLFS_E_TIMEOUT). */
+typedef struct {
+    int32_t cycle;
+    int32_t port;
+    uint8_t detected;
+    uint8_t reserved[3];
+} rtlfs_result;
+
+/* ---- run options ---------------------------------------------------------------------- */
+#define RTLFS_SCHED_PLAIN      0   /* queue in fault-list order, no heavy pre-assignment */
+#define RTLFS_SCHED_HEURISTIC  1   /* order by static cone size x toggle rate */
+#define RTLFS_SCHED_MLP        2   /* order by the load predictor (falls back to heuristic
+                                      when no weights are loaded) */
+
+typedef struct {
+    int32_t  scheduler;      /* RTLFS_SCHED_*; default HEURISTIC */
+    int32_t  light_block;    /* threads per CTA of the light kernel (32..1024); 0 = auto */
+    int32_t  heavy_block;    /* threads per CTA of the heavy kernel (32..1024); 0 = auto */
+    int32_t  heavy_ctas;     /* resident heavy CTAs (scratch slots); 0 = auto */
+    float    heavy_frac;     /* fraction of faults (highest predicted load) sent to the
+                                heavy kernel from cycle 0; < 0 = auto */
+    int32_t  use_graph;      /* 1 = capture the launch sequence in a CUDA graph and replay */
+    uint64_t fault_budget;   /* max node evaluations per fault, 0 = unlimited */
+    uint32_t reserved[8];
+} rtlfs_run_opts;
+
+/* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */
+typedef struct {
+    double   total_ms;       /* first launch to results on host */
+    double   good_ms;        /* good-machine trace (all designs) */
+    double   prep_ms;        /* features, predictor, queue order */
+    double   faulty_ms;      /* light + heavy faulty-machine kernels */
+    double   light_ms;       /* light kernel alone */
+    double   heavy_ms;       /* promoted-fault heavy pass alone */
+    uint64_t fault_cycles;   /* W = sum over faults of (cycle+1 if detected else T) */
+    uint64_t node_evals;     /* sum of the per-fault propagation loads */
+    uint64_t promoted;       /* light faults promoted to the heavy kernel */
+    uint64_t heavy_initial;  /* faults assigned to the heavy kernel from cycle 0 */
+    uint32_t n_launches;     /* kernels launched by the run */
+    uint32_t reserved[7];
+} rtlfs_stats;
+
+typedef struct rtlfs_ctx rtlfs_ctx;   /* opaque */
+
+/* Create a context on CUDA device `device`. *out receives the handle. Errors:
+ * RTLFS_E_ARG (null out / bad device), RTLFS_E_CUDA. */
+int rtlfs_create(rtlfs_ctx **out, int device);
+
+/* Free every device and host resource of the context. Null is accepted. */
+void rtlfs_destroy(rtlfs_ctx *ctx);
+
+/* One-line description of the last error on this context ("" after success). */
+const char *rtlfs_last_error(const rtlfs_ctx *ctx);
+
+/* Load one design (Sec. II-B: the RTL graph; Sec. IV, Steps 1-4: compile, inject,
+ * build the task graph): nodes[n_nodes], regs[n_regs], input_widths[n_inputs] (1..64),
+ * output_nets[n_outputs] (port o observes net output_nets[o]). The library validates
+ * ids and width rules, rejects combinational cycles (RTLFS_E_CYCLE; registers break
+ * cycles), levelizes the nodes, builds fan-out and latch maps and uploads them. The new
+ * design's id (0, 1, ... in load order) goes to *design_id. All designs of a context run
+ * together in rtlfs_run. Errors: RTLFS_E_ARG, RTLFS_E_WIDTH, RTLFS_E_CYCLE, RTLFS_E_NOMEM. */
+int rtlfs_load_design(rtlfs_ctx *ctx, const rtlfs_node *nodes, uint32_t n_nodes,
+                      const rtlfs_reg *regs, uint32_t n_regs,
+                      const uint8_t *input_widths, uint32_t n_inputs,
+                      const uint32_t *output_nets, uint32_t n_outputs,
+                      uint32_t *design_id);
+
+/* Stimulus of a design: inputs[n_cycles][n_inputs] row-major; each value is masked to
+ * its input's width on use. 1 <= n_cycles <= 2^21. Replaces an earlier stimulus. Errors:
+ * RTLFS_E_ARG, RTLFS_E_NOMEM. */
+int rtlfs_set_stimulus(rtlfs_ctx *ctx, uint32_t design_id, const uint64_t *inputs,
+                       uint32_t n_cycles);
+
+/* Fault list of a design: faults[n_faults] (n_faults may be 0). Each fault's bit must
+ * be below its net's width (RTLFS_E_ARG otherwise). Duplicates are simulated
+ * independently. Replaces an earlier list. Errors: RTLFS_E_ARG, RTLFS_E_NOMEM. */
+int rtlfs_set_faults(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults,
+                     uint32_t n_faults);
+
+/* Simulate every loaded design's fault list under its stimulus (the whole hot path: good
+ * trace, load prediction and queue order, light and heavy faulty machines with output
+ * compare, fault dropping and register latch). out_per_design[d] is a caller buffer of
+ * n_faults(d) results in the design's fault-list order; out_load_per_design may be null
+ * or hold per-design buffers (entries may be null) of n_faults(d) uint64 propagation
+ * loads (node evaluations summed over the cycles the fault was simulated). opts may be
+ * null (defaults). Results never depend on the options. Errors: RTLFS_E_STATE (a design
+ * without stimulus), RTLFS_E_ARG, RTLFS_E_CUDA, RTLFS_E_TIMEOUT (fault_budget ran out;
+ * the affected results carry detected = 255, the others are valid). */
+int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts,
+              rtlfs_result *const *out_per_design, uint64_t *const *out_load_per_design);
+
+/* The plain GPU form: one thread per fault, one flat launch per design, no queue, no
+ * heavy path, no prediction; same result contract as rtlfs_run. */
+int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out_per_design);
+
+/* Counters and timings of the last rtlfs_run / rtlfs_run_plain. */
+int rtlfs_get_stats(const rtlfs_ctx *ctx, rtlfs_stats *out);
+
+/* Test hooks: the good machine's outputs out[n_cycles][n_outputs], or every net's value
+ * out[n_cycles][n_nets] in the caller's net numbering, as computed by the last run (or
+ * by a good-trace-only run if none happened since the stimulus was set). */
+int rtlfs_good_outputs(rtlfs_ctx *ctx, uint32_t design_id, uint64_t *out);
+int rtlfs_good_trace(rtlfs_ctx *ctx, uint32_t design_id, uint64_t *out);
+
+/* Design sizes after load: n_nets, number of topological levels, total fan-out edges. */
+int rtlfs_design_info(const rtlfs_ctx *ctx, uint32_t design_id, uint32_t *n_nets,
+                      uint32_t *n_levels, uint32_t *n_fanout_edges);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTLFS_H */

@@ -1,0 +1,867 @@
+// rtlfs_host.cu -- host side of librtlfs: the C ABI declared in include/rtlfs.h.
+//
+// Load time (the paper's compile / inject / task-graph steps, Sec. IV Steps 1-4, here
+// for a word-level op graph): validate, levelize, renumber nodes by level, build the
+// fan-out CSR (successor updates of Algorithm 1), the register latch map and the output
+// map, and upload them. Run time: good trace, schedule, light + heavy faulty kernels on
+// two streams, results back to the caller.
+#include "../../include/rtlfs.h"
+#include "rtlfs_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace rtlfs;
+
+namespace {
+
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t reserve(size_t count) {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        n = std::max<size_t>(count, 1);
+        return cudaSuccess;
+    }
+    cudaError_t upload(const std::vector<T> &v) {
+        cudaError_t e = reserve(v.size());
+        if (e != cudaSuccess) return e;
+        if (v.empty()) return cudaSuccess;
+        return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    }
+};
+
+struct Design {
+    uint32_t I = 0, R = 0, N = 0, O = 0, n_net = 0, n_levels = 0, n_fo = 0;
+    std::vector<uint32_t> ext2int, int2ext;
+    std::vector<uint4> desc;
+    std::vector<uint32_t> lvl_start;
+    std::vector<uint16_t> node_level;
+    std::vector<uint8_t> net_w;
+    std::vector<uint32_t> fo_off, fo_idx, dreg_off, dreg_idx, reg_d, outport, out_net;
+    std::vector<float> cone;          // static fan-out cone size estimate per net (log2 scale)
+    DBuf<uint4> d_desc;
+    DBuf<uint32_t> d_lvl_start, d_fo_off, d_fo_idx, d_dreg_off, d_dreg_idx, d_reg_d, d_outport,
+        d_out_net;
+    DBuf<uint16_t> d_node_level;
+    DBuf<uint8_t> d_net_w;
+    // stimulus and faults
+    uint32_t T = 0;
+    bool has_stim = false;
+    DBuf<uint64_t> d_stim;
+    std::vector<uint32_t> f_site;     // internal ids
+    std::vector<uint8_t> f_bit, f_val;
+    // good trace
+    DBuf<uint64_t> d_rows, d_gcol;
+    bool trace_valid = false;
+};
+
+}  // namespace
+
+struct rtlfs_ctx {
+    int device = 0;
+    int n_sm = 0;
+    std::string err;
+    std::vector<Design *> designs;
+    cudaStream_t s_main = nullptr, s_heavy = nullptr;
+    cudaEvent_t ev[8] = {};
+    DBuf<DevDesign> d_designs;
+    DBuf<uint32_t> d_list_smem, d_list_glob;
+    bool faults_dirty = true;
+    uint32_t F = 0;
+    std::vector<uint32_t> f_first;    // first global fault id of each design
+    DBuf<uint32_t> d_site;
+    DBuf<uint8_t> d_bit, d_val, d_det;
+    DBuf<uint16_t> d_fdesign;
+    DBuf<int32_t> d_cycle, d_port;
+    DBuf<uint64_t> d_load;
+    DBuf<uint32_t> d_order;
+    DBuf<HeavyItem> d_init_items, d_prom_items;
+    DBuf<uint32_t> d_counters;        // [0] init count, [1] prom count
+    DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget
+    DBuf<uint64_t> h_fval;
+    DBuf<uint32_t> h_stamp, h_epoch, h_regr;
+    DBuf<uint64_t> h_regv;
+    uint32_t heavy_slots = 0, heavy_grid = 0, hs_net = 0, hs_reg = 0, hs_node = 0, hs_lv = 0;
+    // pinned host staging of results
+    int32_t *p_cycle = nullptr, *p_port = nullptr;
+    uint8_t *p_det = nullptr;
+    uint64_t *p_load = nullptr;
+    size_t p_cap = 0;
+    rtlfs_stats stats{};
+};
+
+namespace {
+
+int fail(rtlfs_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CU(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? RTLFS_E_NOMEM : RTLFS_E_CUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                          \
+    } while (0)
+
+inline int n_ops(uint32_t op) {
+    return op == OP_CONST ? 0
+         : (op == OP_NOT || op == OP_SHL || op == OP_SHR || op == OP_SLICE) ? 1
+         : op == OP_MUX2 ? 3 : 2;
+}
+
+inline uint64_t host_mask(uint32_t w) { return w >= 64 ? ~0ull : ((1ull << w) - 1ull); }
+
+int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
+                 const rtlfs_reg *regs, uint32_t R, const uint8_t *in_w, uint32_t I,
+                 const uint32_t *outs, uint32_t O) {
+    const uint64_t n_net64 = (uint64_t)I + R + N;
+    if (n_net64 == 0 || n_net64 >= (1ull << 31)) return fail(ctx, RTLFS_E_ARG, "bad net count");
+    const uint32_t n_net = (uint32_t)n_net64, IR = I + R;
+    std::vector<uint8_t> wext(n_net);
+    for (uint32_t i = 0; i < I; ++i) {
+        if (in_w[i] < 1 || in_w[i] > 64) return fail(ctx, RTLFS_E_WIDTH, "input %u width %u", i, in_w[i]);
+        wext[i] = in_w[i];
+    }
+    for (uint32_t r = 0; r < R; ++r) {
+        if (regs[r].width < 1 || regs[r].width > 64)
+            return fail(ctx, RTLFS_E_WIDTH, "register %u width %u", r, regs[r].width);
+        if (regs[r].d_net >= n_net) return fail(ctx, RTLFS_E_ARG, "register %u d_net out of range", r);
+        wext[I + r] = regs[r].width;
+    }
+    for (uint32_t n = 0; n < N; ++n) {
+        const rtlfs_node &x = nodes[n];
+        if (x.op > OP_CONST) return fail(ctx, RTLFS_E_ARG, "node %u: bad op %u", n, x.op);
+        if (x.width < 1 || x.width > 64) return fail(ctx, RTLFS_E_WIDTH, "node %u width %u", n, x.width);
+        const uint32_t ops[3] = {x.a, x.b, x.c};
+        for (int k = 0; k < n_ops(x.op); ++k)
+            if (ops[k] >= n_net) return fail(ctx, RTLFS_E_ARG, "node %u operand %d out of range", n, k);
+        wext[IR + n] = x.width;
+    }
+    for (uint32_t n = 0; n < N; ++n) {
+        const rtlfs_node &x = nodes[n];
+        if ((x.op == OP_EQ || x.op == OP_LT) && x.width != 1)
+            return fail(ctx, RTLFS_E_WIDTH, "node %u: EQ/LT width must be 1", n);
+        if (x.op == OP_SLICE && (uint64_t)x.imm + x.width > wext[x.a])
+            return fail(ctx, RTLFS_E_WIDTH, "node %u: slice beyond operand width", n);
+        if (x.op == OP_CONCAT && (uint32_t)wext[x.a] + wext[x.b] != x.width)
+            return fail(ctx, RTLFS_E_WIDTH, "node %u: concat width mismatch", n);
+    }
+    for (uint32_t o = 0; o < O; ++o)
+        if (outs[o] >= n_net) return fail(ctx, RTLFS_E_ARG, "output %u net out of range", o);
+
+    // Levelize (Kahn over node->node operand edges); level 0 = no node operand.
+    std::vector<uint32_t> indeg(N, 0), ucnt(N + 1, 0);
+    for (uint32_t n = 0; n < N; ++n) {
+        const uint32_t ops[3] = {nodes[n].a, nodes[n].b, nodes[n].c};
+        for (int k = 0; k < n_ops(nodes[n].op); ++k)
+            if (ops[k] >= IR) { ++indeg[n]; ++ucnt[ops[k] - IR + 1]; }
+    }
+    for (uint32_t n = 0; n < N; ++n) ucnt[n + 1] += ucnt[n];
+    std::vector<uint32_t> users(ucnt[N]), fill(ucnt.begin(), ucnt.end() - 1);
+    for (uint32_t n = 0; n < N; ++n) {
+        const uint32_t ops[3] = {nodes[n].a, nodes[n].b, nodes[n].c};
+        for (int k = 0; k < n_ops(nodes[n].op); ++k)
+            if (ops[k] >= IR) users[fill[ops[k] - IR]++] = n;
+    }
+    std::vector<uint32_t> level(N, 0), queue;
+    queue.reserve(N);
+    for (uint32_t n = 0; n < N; ++n)
+        if (indeg[n] == 0) queue.push_back(n);
+    for (size_t h = 0; h < queue.size(); ++h) {
+        const uint32_t n = queue[h];
+        for (uint32_t e = ucnt[n]; e < ucnt[n + 1]; ++e) {
+            const uint32_t u = users[e];
+            level[u] = std::max(level[u], level[n] + 1);
+            if (--indeg[u] == 0) queue.push_back(u);
+        }
+    }
+    if (queue.size() != N) return fail(ctx, RTLFS_E_CYCLE, "combinational cycle among nodes");
+    uint32_t NL = 0;
+    for (uint32_t n = 0; n < N; ++n) NL = std::max(NL, level[n] + 1);
+    if (N == 0) NL = 0;
+    if (NL > 65535) return fail(ctx, RTLFS_E_ARG, "more than 65535 levels");
+
+    // Renumber: nodes sorted by (level, index).
+    D.I = I; D.R = R; D.N = N; D.O = O; D.n_net = n_net; D.n_levels = NL;
+    D.lvl_start.assign(NL + 1, 0);
+    for (uint32_t n = 0; n < N; ++n) ++D.lvl_start[level[n] + 1];
+    for (uint32_t l = 0; l < NL; ++l) D.lvl_start[l + 1] += D.lvl_start[l];
+    std::vector<uint32_t> pos(D.lvl_start.begin(), D.lvl_start.end());
+    D.ext2int.resize(n_net);
+    D.int2ext.resize(n_net);
+    for (uint32_t i = 0; i < IR; ++i) D.ext2int[i] = D.int2ext[i] = i;
+    D.node_level.resize(N);
+    for (uint32_t n = 0; n < N; ++n) {
+        const uint32_t k = pos[level[n]]++;
+        D.ext2int[IR + n] = IR + k;
+        D.int2ext[IR + k] = IR + n;
+        D.node_level[k] = (uint16_t)level[n];
+    }
+    D.net_w.resize(n_net);
+    for (uint32_t e = 0; e < n_net; ++e) D.net_w[D.ext2int[e]] = wext[e];
+    D.desc.resize(N);
+    for (uint32_t n = 0; n < N; ++n) {
+        const rtlfs_node &x = nodes[n];
+        const uint32_t k = D.ext2int[IR + n] - IR;
+        uint4 d;
+        if (x.op == OP_CONST) {
+            const uint64_t v = x.imm & host_mask(x.width);
+            d.x = (uint32_t)v;
+            d.y = (uint32_t)(v >> 32);
+            d.z = 0;
+        } else {
+            const int no = n_ops(x.op);
+            d.x = D.ext2int[x.a];
+            d.y = no >= 2 ? D.ext2int[x.b] : 0;
+            d.z = no >= 3 ? D.ext2int[x.c] : 0;
+        }
+        uint32_t kk = 0;
+        if (x.op == OP_SHL || x.op == OP_SHR || x.op == OP_SLICE) kk = (uint32_t)std::min<uint64_t>(x.imm, 64);
+        if (x.op == OP_CONCAT) kk = wext[x.b];
+        d.w = make_meta(x.op, x.width, kk);
+        D.desc[k] = d;
+    }
+    // Fan-out CSR over internal nets (each consumer once per distinct operand net).
+    D.fo_off.assign(n_net + 1, 0);
+    for (uint32_t k = 0; k < N; ++k) {
+        const uint4 d = D.desc[k];
+        const int no = n_ops(meta_op(d.w));
+        const uint32_t ops[3] = {d.x, d.y, d.z};
+        for (int j = 0; j < no; ++j) {
+            bool dup = false;
+            for (int i = 0; i < j; ++i) dup |= ops[i] == ops[j];
+            if (!dup) ++D.fo_off[ops[j] + 1];
+        }
+    }
+    for (uint32_t e = 0; e < n_net; ++e) D.fo_off[e + 1] += D.fo_off[e];
+    D.n_fo = D.fo_off[n_net];
+    D.fo_idx.resize(D.n_fo);
+    {
+        std::vector<uint32_t> f2(D.fo_off.begin(), D.fo_off.end() - 1);
+        for (uint32_t k = 0; k < N; ++k) {
+            const uint4 d = D.desc[k];
+            const int no = n_ops(meta_op(d.w));
+            const uint32_t ops[3] = {d.x, d.y, d.z};
+            for (int j = 0; j < no; ++j) {
+                bool dup = false;
+                for (int i = 0; i < j; ++i) dup |= ops[i] == ops[j];
+                if (!dup) D.fo_idx[f2[ops[j]]++] = k;
+            }
+        }
+    }
+    // Latch map: registers whose D is each net.
+    D.reg_d.resize(R);
+    D.dreg_off.assign(n_net + 1, 0);
+    for (uint32_t r = 0; r < R; ++r) {
+        D.reg_d[r] = D.ext2int[regs[r].d_net];
+        ++D.dreg_off[D.reg_d[r] + 1];
+    }
+    for (uint32_t e = 0; e < n_net; ++e) D.dreg_off[e + 1] += D.dreg_off[e];
+    D.dreg_idx.resize(R);
+    {
+        std::vector<uint32_t> f2(D.dreg_off.begin(), D.dreg_off.end() - 1);
+        for (uint32_t r = 0; r < R; ++r) D.dreg_idx[f2[D.reg_d[r]]++] = r;
+    }
+    // Outputs.
+    D.out_net.resize(O);
+    D.outport.assign(n_net, NO_PORT);
+    for (uint32_t o = 0; o < O; ++o) {
+        const uint32_t net = D.ext2int[outs[o]];
+        D.out_net[o] = net;
+        D.outport[net] = std::min(D.outport[net], o);
+    }
+    // Static fan-out cone estimate (reverse topological sum, capped): scheduling feature.
+    D.cone.assign(n_net, 0.f);
+    {
+        std::vector<double> cs(n_net, 1.0);
+        for (int64_t k = (int64_t)N - 1; k >= 0; --k) {
+            const uint32_t net = IR + (uint32_t)k;
+            double s = 1.0;
+            for (uint32_t e = D.fo_off[net]; e < D.fo_off[net + 1]; ++e) s += cs[IR + D.fo_idx[e]];
+            cs[net] = std::min(s, 1e9);
+        }
+        for (uint32_t net = 0; net < IR; ++net) {
+            double s = 1.0;
+            for (uint32_t e = D.fo_off[net]; e < D.fo_off[net + 1]; ++e) s += cs[IR + D.fo_idx[e]];
+            cs[net] = std::min(s, 1e9);
+        }
+        for (uint32_t e = 0; e < n_net; ++e) D.cone[e] = (float)std::log2(cs[e]);
+    }
+    return RTLFS_OK;
+}
+
+int upload_design(rtlfs_ctx *ctx, Design &D) {
+    CU(D.d_desc.upload(D.desc));
+    CU(D.d_lvl_start.upload(D.lvl_start));
+    CU(D.d_node_level.upload(D.node_level));
+    CU(D.d_net_w.upload(D.net_w));
+    CU(D.d_fo_off.upload(D.fo_off));
+    CU(D.d_fo_idx.upload(D.fo_idx));
+    CU(D.d_dreg_off.upload(D.dreg_off));
+    CU(D.d_dreg_idx.upload(D.dreg_idx));
+    CU(D.d_reg_d.upload(D.reg_d));
+    CU(D.d_outport.upload(D.outport));
+    CU(D.d_out_net.upload(D.out_net));
+    return RTLFS_OK;
+}
+
+DevDesign dev_view(const Design &D) {
+    DevDesign v{};
+    v.I = D.I; v.R = D.R; v.N = D.N; v.O = D.O; v.n_net = D.n_net; v.n_levels = D.n_levels;
+    v.T = D.T; v.n_fo = D.n_fo;
+    v.desc = D.d_desc.p; v.lvl_start = D.d_lvl_start.p; v.node_level = D.d_node_level.p;
+    v.net_w = D.d_net_w.p; v.fo_off = D.d_fo_off.p; v.fo_idx = D.d_fo_idx.p;
+    v.dreg_off = D.d_dreg_off.p; v.dreg_idx = D.d_dreg_idx.p; v.reg_d = D.d_reg_d.p;
+    v.outport = D.d_outport.p; v.out_net = D.d_out_net.p; v.stim = D.d_stim.p;
+    v.rows = D.d_rows.p; v.gcol = D.d_gcol.p;
+    return v;
+}
+
+constexpr size_t SMEM_LIMIT = 200 * 1024;   // good-trace values in shared memory up to this
+
+// Allocate traces, upload the design table, enqueue good trace + transposes on s_main.
+int enqueue_good(rtlfs_ctx *ctx) {
+    std::vector<DevDesign> tab;
+    std::vector<uint32_t> l_smem, l_glob;
+    uint32_t max_net_s = 0, max_reg_s = 0;
+    for (size_t i = 0; i < ctx->designs.size(); ++i) {
+        Design &D = *ctx->designs[i];
+        const size_t cells = (size_t)D.n_net * D.T;
+        CU(D.d_rows.reserve(cells));
+        CU(D.d_gcol.reserve(cells));
+        tab.push_back(dev_view(D));
+        const size_t smem = ((size_t)D.n_net + D.R) * sizeof(uint64_t);
+        if (smem <= SMEM_LIMIT) {
+            l_smem.push_back((uint32_t)i);
+            max_net_s = std::max(max_net_s, D.n_net);
+            max_reg_s = std::max(max_reg_s, D.R);
+        } else {
+            l_glob.push_back((uint32_t)i);
+        }
+    }
+    CU(ctx->d_designs.upload(tab));
+    CU(ctx->d_list_smem.upload(l_smem));
+    CU(ctx->d_list_glob.upload(l_glob));
+    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, (uint32_t)l_smem.size(), max_net_s,
+                         max_reg_s, true, ctx->s_main));
+    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, (uint32_t)l_glob.size(), 0, 0,
+                         false, ctx->s_main));
+    for (Design *D : ctx->designs)
+        CU(launch_transpose(D->d_gcol.p, D->d_rows.p, D->n_net, D->T, ctx->s_main));
+    return RTLFS_OK;
+}
+
+int build_faults(rtlfs_ctx *ctx) {
+    if (!ctx->faults_dirty) return RTLFS_OK;
+    std::vector<uint32_t> site;
+    std::vector<uint8_t> bit, val;
+    std::vector<uint16_t> des;
+    ctx->f_first.clear();
+    for (size_t i = 0; i < ctx->designs.size(); ++i) {
+        Design &D = *ctx->designs[i];
+        ctx->f_first.push_back((uint32_t)site.size());
+        site.insert(site.end(), D.f_site.begin(), D.f_site.end());
+        bit.insert(bit.end(), D.f_bit.begin(), D.f_bit.end());
+        val.insert(val.end(), D.f_val.begin(), D.f_val.end());
+        des.insert(des.end(), D.f_site.size(), (uint16_t)i);
+    }
+    ctx->f_first.push_back((uint32_t)site.size());
+    ctx->F = (uint32_t)site.size();
+    CU(ctx->d_site.upload(site));
+    CU(ctx->d_bit.upload(bit));
+    CU(ctx->d_val.upload(val));
+    CU(ctx->d_fdesign.upload(des));
+    CU(ctx->d_cycle.reserve(ctx->F));
+    CU(ctx->d_port.reserve(ctx->F));
+    CU(ctx->d_det.reserve(ctx->F));
+    CU(ctx->d_load.reserve(ctx->F));
+    CU(ctx->d_order.reserve(ctx->F));
+    CU(ctx->d_prom_items.reserve(ctx->F));
+    CU(ctx->d_init_items.reserve(ctx->F));
+    if (ctx->p_cap < ctx->F || !ctx->p_cycle) {
+        if (ctx->p_cycle) { cudaFreeHost(ctx->p_cycle); cudaFreeHost(ctx->p_port); cudaFreeHost(ctx->p_det); cudaFreeHost(ctx->p_load); }
+        const size_t n = std::max<size_t>(ctx->F, 1);
+        CU(cudaMallocHost(&ctx->p_cycle, n * sizeof(int32_t)));
+        CU(cudaMallocHost(&ctx->p_port, n * sizeof(int32_t)));
+        CU(cudaMallocHost(&ctx->p_det, n));
+        CU(cudaMallocHost(&ctx->p_load, n * sizeof(uint64_t)));
+        ctx->p_cap = n;
+    }
+    ctx->faults_dirty = false;
+    return RTLFS_OK;
+}
+
+DevFaults dev_faults(rtlfs_ctx *ctx) {
+    DevFaults f{};
+    f.F = ctx->F;
+    f.site = ctx->d_site.p; f.bit = ctx->d_bit.p; f.val = ctx->d_val.p; f.design = ctx->d_fdesign.p;
+    f.res_cycle = ctx->d_cycle.p; f.res_port = ctx->d_port.p; f.res_det = ctx->d_det.p;
+    f.load = ctx->d_load.p;
+    return f;
+}
+
+int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots) {
+    uint32_t mn = 1, mr = 1, mnode = 1, ml = 1;
+    for (Design *D : ctx->designs) {
+        mn = std::max(mn, D->n_net); mr = std::max(mr, D->R);
+        mnode = std::max(mnode, D->N); ml = std::max(ml, D->n_levels);
+    }
+    const size_t smem = heavy_smem_bytes(mnode, ml);
+    if (smem > 220 * 1024) return fail(ctx, RTLFS_E_ARG, "design too large for the heavy kernel bitmap");
+    int per_sm = heavy_max_blocks_per_sm(block, smem);
+    if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "heavy kernel cannot be resident with block %d", block);
+    int slots = want_slots > 0 ? want_slots : per_sm * ctx->n_sm;
+    slots = std::min(slots, per_sm * ctx->n_sm);
+    const bool grow = slots > (int)ctx->heavy_slots || mn > ctx->hs_net || mr > ctx->hs_reg;
+    if (grow) {
+        ctx->h_fval.release(); ctx->h_stamp.release(); ctx->h_epoch.release();
+        ctx->h_regr.release(); ctx->h_regv.release();
+        CU(ctx->h_fval.reserve((size_t)slots * mn));
+        CU(ctx->h_stamp.reserve((size_t)slots * mn));
+        CU(ctx->h_epoch.reserve(slots));
+        CU(ctx->h_regr.reserve((size_t)slots * 2 * mr));
+        CU(ctx->h_regv.reserve((size_t)slots * 2 * mr));
+        CU(cudaMemset(ctx->h_stamp.p, 0, (size_t)slots * mn * sizeof(uint32_t)));
+        CU(cudaMemset(ctx->h_epoch.p, 0, (size_t)slots * sizeof(uint32_t)));
+        ctx->heavy_slots = slots; ctx->hs_net = mn; ctx->hs_reg = mr;
+    }
+    ctx->hs_node = mnode; ctx->hs_lv = ml;
+    ctx->heavy_grid = (uint32_t)slots;
+    return RTLFS_OK;
+}
+
+HeavyScratch heavy_view(rtlfs_ctx *ctx) {
+    HeavyScratch s{};
+    s.fval = ctx->h_fval.p; s.stamp = ctx->h_stamp.p; s.epoch = ctx->h_epoch.p;
+    s.reg_r = ctx->h_regr.p; s.reg_v = ctx->h_regv.p;
+    s.max_net = ctx->hs_net; s.max_reg = ctx->hs_reg; s.max_node = ctx->hs_node;
+    s.max_levels = ctx->hs_lv;
+    return s;
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+    return ms;
+}
+
+}  // namespace
+
+// ---- ABI ------------------------------------------------------------------------------
+
+extern "C" {
+
+int rtlfs_create(rtlfs_ctx **out, int device) {
+    rtlfs_ctx *ctx = nullptr;
+    if (!out) return RTLFS_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return RTLFS_E_ARG;
+    ctx = new rtlfs_ctx();
+    ctx->device = device;
+    int rc = RTLFS_OK;
+    auto init = [&]() -> int {
+        CU(cudaSetDevice(device));
+        CU(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device));
+        CU(cudaStreamCreateWithFlags(&ctx->s_main, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&ctx->s_heavy, cudaStreamNonBlocking));
+        for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
+        CU(ctx->d_counters.reserve(4));
+        CU(ctx->d_heads.reserve(4));
+        return RTLFS_OK;
+    };
+    rc = init();
+    if (rc != RTLFS_OK) { rtlfs_destroy(ctx); return rc; }
+    *out = ctx;
+    return RTLFS_OK;
+}
+
+void rtlfs_destroy(rtlfs_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->s_main) cudaStreamSynchronize(ctx->s_main);
+    if (ctx->s_heavy) cudaStreamSynchronize(ctx->s_heavy);
+    for (Design *D : ctx->designs) delete D;
+    ctx->designs.clear();
+    for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+    if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
+    if (ctx->s_heavy) cudaStreamDestroy(ctx->s_heavy);
+    if (ctx->p_cycle) { cudaFreeHost(ctx->p_cycle); cudaFreeHost(ctx->p_port); cudaFreeHost(ctx->p_det); cudaFreeHost(ctx->p_load); }
+    delete ctx;
+}
+
+const char *rtlfs_last_error(const rtlfs_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rtlfs_load_design(rtlfs_ctx *ctx, const rtlfs_node *nodes, uint32_t n_nodes,
+                      const rtlfs_reg *regs, uint32_t n_regs, const uint8_t *input_widths,
+                      uint32_t n_inputs, const uint32_t *output_nets, uint32_t n_outputs,
+                      uint32_t *design_id) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!design_id || (n_nodes && !nodes) || (n_regs && !regs) || (n_inputs && !input_widths) ||
+        (n_outputs && !output_nets))
+        return fail(ctx, RTLFS_E_ARG, "null array with nonzero size");
+    if (ctx->designs.size() >= 65535) return fail(ctx, RTLFS_E_ARG, "too many designs");
+    CU(cudaSetDevice(ctx->device));
+    Design *D = new Design();
+    int rc = build_design(ctx, *D, nodes, n_nodes, regs, n_regs, input_widths, n_inputs,
+                          output_nets, n_outputs);
+    if (rc == RTLFS_OK) rc = upload_design(ctx, *D);
+    if (rc != RTLFS_OK) { delete D; return rc; }
+    *design_id = (uint32_t)ctx->designs.size();
+    ctx->designs.push_back(D);
+    ctx->faults_dirty = true;
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+int rtlfs_set_stimulus(rtlfs_ctx *ctx, uint32_t design_id, const uint64_t *inputs, uint32_t n_cycles) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size()) return fail(ctx, RTLFS_E_ARG, "bad design id");
+    Design &D = *ctx->designs[design_id];
+    if (n_cycles < 1 || n_cycles > (1u << 21)) return fail(ctx, RTLFS_E_ARG, "n_cycles out of range (1..2^21)");
+    if (D.I && !inputs) return fail(ctx, RTLFS_E_ARG, "null inputs");
+    if ((size_t)D.n_net * n_cycles > (1ull << 36)) return fail(ctx, RTLFS_E_ARG, "trace too large");
+    CU(cudaSetDevice(ctx->device));
+    const size_t cells = (size_t)n_cycles * D.I;
+    CU(D.d_stim.reserve(cells));
+    if (cells) CU(cudaMemcpy(D.d_stim.p, inputs, cells * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    D.T = n_cycles;
+    D.has_stim = true;
+    D.trace_valid = false;
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+int rtlfs_set_faults(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults, uint32_t n_faults) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size()) return fail(ctx, RTLFS_E_ARG, "bad design id");
+    if (n_faults && !faults) return fail(ctx, RTLFS_E_ARG, "null faults");
+    Design &D = *ctx->designs[design_id];
+    std::vector<uint32_t> s(n_faults);
+    std::vector<uint8_t> b(n_faults), v(n_faults);
+    for (uint32_t i = 0; i < n_faults; ++i) {
+        const rtlfs_fault &x = faults[i];
+        if (x.net >= D.n_net) return fail(ctx, RTLFS_E_ARG, "fault %u: net out of range", i);
+        const uint32_t in = D.ext2int[x.net];
+        if (x.bit >= D.net_w[in]) return fail(ctx, RTLFS_E_ARG, "fault %u: bit beyond net width", i);
+        if (x.stuck > 1) return fail(ctx, RTLFS_E_ARG, "fault %u: stuck value must be 0 or 1", i);
+        s[i] = in; b[i] = x.bit; v[i] = x.stuck;
+    }
+    D.f_site.swap(s); D.f_bit.swap(b); D.f_val.swap(v);
+    ctx->faults_dirty = true;
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+static int run_good_only(rtlfs_ctx *ctx) {
+    for (Design *D : ctx->designs)
+        if (!D->has_stim) return fail(ctx, RTLFS_E_STATE, "a design has no stimulus");
+    int rc = enqueue_good(ctx);
+    if (rc != RTLFS_OK) return rc;
+    CU(cudaStreamSynchronize(ctx->s_main));
+    for (Design *D : ctx->designs) D->trace_valid = true;
+    return RTLFS_OK;
+}
+
+int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const *out,
+              uint64_t *const *out_load) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (ctx->designs.empty()) return fail(ctx, RTLFS_E_STATE, "no design loaded");
+    if (!out) return fail(ctx, RTLFS_E_ARG, "null result array");
+    for (Design *D : ctx->designs)
+        if (!D->has_stim) return fail(ctx, RTLFS_E_STATE, "a design has no stimulus");
+    rtlfs_run_opts o{};
+    o.scheduler = RTLFS_SCHED_HEURISTIC;
+    o.heavy_frac = -1.f;
+    if (opts_in) o = *opts_in;
+    const int lblock = o.light_block > 0 ? o.light_block : 128;
+    const int hblock = o.heavy_block > 0 ? o.heavy_block : 128;
+    if (lblock < 32 || lblock > 256 || (lblock & 31)) return fail(ctx, RTLFS_E_ARG, "light_block must be a multiple of 32 in 32..256");
+    if (hblock < 32 || hblock > 1024 || (hblock & 31)) return fail(ctx, RTLFS_E_ARG, "heavy_block must be a multiple of 32 in 32..1024");
+    CU(cudaSetDevice(ctx->device));
+    const auto t_host0 = std::chrono::steady_clock::now();
+    int rc = build_faults(ctx);
+    if (rc != RTLFS_OK) return rc;
+    const uint32_t F = ctx->F;
+
+    // Schedule: queue order and heavy pre-assignment (host side).
+    std::vector<uint32_t> order(F);
+    for (uint32_t i = 0; i < F; ++i) order[i] = i;
+    std::vector<HeavyItem> init;
+    if (o.scheduler != RTLFS_SCHED_PLAIN && F) {
+        std::vector<float> score(F);
+        for (size_t d = 0; d < ctx->designs.size(); ++d) {
+            Design &D = *ctx->designs[d];
+            for (uint32_t i = ctx->f_first[d]; i < ctx->f_first[d + 1]; ++i)
+                score[i] = D.cone[D.f_site[i - ctx->f_first[d]]];
+        }
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return score[a] > score[b]; });
+        const float hf = o.heavy_frac >= 0.f ? std::min(o.heavy_frac, 1.f) : 0.0f;
+        const uint32_t nh = (uint32_t)(hf * F);
+        for (uint32_t i = 0; i < nh; ++i) {
+            HeavyItem h{};
+            h.fault = order[i];
+            init.push_back(h);
+        }
+        order.erase(order.begin(), order.begin() + nh);
+    }
+    CU(ctx->d_order.upload(order));
+    if (!init.empty()) CU(cudaMemcpy(ctx->d_init_items.p, init.data(), init.size() * sizeof(HeavyItem), cudaMemcpyHostToDevice));
+    const uint32_t counters[4] = {(uint32_t)init.size(), 0u, 0u, 0u};
+    CU(cudaMemcpy(ctx->d_counters.p, counters, sizeof(counters), cudaMemcpyHostToDevice));
+    rc = ensure_heavy_scratch(ctx, hblock, o.heavy_ctas);
+    if (rc != RTLFS_OK) return rc;
+    const auto t_host1 = std::chrono::steady_clock::now();
+
+    DevFaults f = dev_faults(ctx);
+    Queues ql{};
+    ql.light_order = ctx->d_order.p;
+    ql.n_light = (uint32_t)order.size();
+    ql.light_head = ctx->d_heads.p + 0;
+    ql.heavy_items = ctx->d_prom_items.p;
+    ql.heavy_count = ctx->d_counters.p + 1;
+    ql.heavy_head = ctx->d_heads.p + 2;
+    ql.heavy_cap = F;
+    ql.budget_hit = ctx->d_heads.p + 3;
+    ql.fault_budget = o.fault_budget;
+    Queues qi = ql;
+    qi.heavy_items = ctx->d_init_items.p;
+    qi.heavy_count = ctx->d_counters.p + 0;
+    qi.heavy_head = ctx->d_heads.p + 1;
+    Queues qp = ql;
+
+    cudaEvent_t *ev = ctx->ev;
+    CU(cudaEventRecord(ev[0], ctx->s_main));
+    CU(cudaMemsetAsync(ctx->d_heads.p, 0, 4 * sizeof(unsigned long long), ctx->s_main));
+    if (F) CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
+    uint32_t launches = 0;
+    rc = enqueue_good(ctx);
+    if (rc != RTLFS_OK) return rc;
+    launches += 2 + (uint32_t)ctx->designs.size();
+    CU(cudaEventRecord(ev[1], ctx->s_main));
+    const int per_sm = light_max_blocks_per_sm(lblock);
+    if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "light kernel cannot be resident");
+    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((ql.n_light + lblock - 1) / lblock,
+                                                                   (int64_t)per_sm * ctx->n_sm));
+    const int hgrid = (int)ctx->heavy_grid;
+    HeavyScratch hs = heavy_view(ctx);
+    if (ql.n_light) { CU(launch_light(ctx->d_designs.p, f, ql, lblock, lgrid, ctx->s_main)); ++launches; }
+    CU(cudaEventRecord(ev[2], ctx->s_main));
+    CU(cudaStreamWaitEvent(ctx->s_heavy, ev[1], 0));
+    if (!init.empty()) { CU(launch_heavy(ctx->d_designs.p, f, qi, hs, hblock, hgrid, ctx->s_heavy)); ++launches; }
+    CU(cudaStreamWaitEvent(ctx->s_heavy, ev[2], 0));
+    CU(cudaEventRecord(ev[3], ctx->s_heavy));
+    CU(launch_heavy(ctx->d_designs.p, f, qp, hs, hblock, hgrid, ctx->s_heavy));
+    ++launches;
+    CU(cudaEventRecord(ev[4], ctx->s_heavy));
+    CU(cudaStreamWaitEvent(ctx->s_main, ev[4], 0));
+    if (F) {
+        CU(cudaMemcpyAsync(ctx->p_cycle, ctx->d_cycle.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_port, ctx->d_port.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
+    }
+    unsigned long long heads[4] = {0, 0, 0, 0};
+    uint32_t cnts[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(heads, ctx->d_heads.p, sizeof(heads), cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaMemcpyAsync(cnts, ctx->d_counters.p, sizeof(cnts), cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaEventRecord(ev[5], ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));
+    for (Design *D : ctx->designs) D->trace_valid = true;
+
+    // Scatter results and counters.
+    rtlfs_stats &st = ctx->stats;
+    st = rtlfs_stats{};
+    st.total_ms = ev_ms(ev[0], ev[5]);
+    st.good_ms = ev_ms(ev[0], ev[1]);
+    st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
+    st.faulty_ms = ev_ms(ev[1], ev[4]);
+    st.light_ms = ev_ms(ev[1], ev[2]);
+    st.heavy_ms = ev_ms(ev[3], ev[4]);
+    st.promoted = cnts[1];
+    st.heavy_initial = cnts[0];
+    st.n_launches = launches;
+    for (size_t d = 0; d < ctx->designs.size(); ++d) {
+        const Design &D = *ctx->designs[d];
+        rtlfs_result *r = out[d];
+        uint64_t *ld = out_load ? out_load[d] : nullptr;
+        for (uint32_t i = ctx->f_first[d]; i < ctx->f_first[d + 1]; ++i) {
+            const uint32_t k = i - ctx->f_first[d];
+            const uint8_t det = ctx->p_det[i];
+            if (r) {
+                r[k].detected = det;
+                r[k].cycle = ctx->p_cycle[i];
+                r[k].port = ctx->p_port[i];
+                r[k].reserved[0] = r[k].reserved[1] = r[k].reserved[2] = 0;
+            }
+            if (ld) ld[k] = ctx->p_load[i];
+            st.node_evals += ctx->p_load[i];
+            if (det == 1) st.fault_cycles += (uint64_t)ctx->p_cycle[i] + 1;
+            else if (det == 0) st.fault_cycles += D.T;
+        }
+    }
+    if (heads[3]) return fail(ctx, RTLFS_E_TIMEOUT, "%llu faults ran out of their work budget", heads[3]);
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (ctx->designs.empty()) return fail(ctx, RTLFS_E_STATE, "no design loaded");
+    if (!out) return fail(ctx, RTLFS_E_ARG, "null result array");
+    for (Design *D : ctx->designs)
+        if (!D->has_stim) return fail(ctx, RTLFS_E_STATE, "a design has no stimulus");
+    CU(cudaSetDevice(ctx->device));
+    int rc = build_faults(ctx);
+    if (rc != RTLFS_OK) return rc;
+    cudaEvent_t *ev = ctx->ev;
+    CU(cudaEventRecord(ev[0], ctx->s_main));
+    rc = enqueue_good(ctx);
+    if (rc != RTLFS_OK) return rc;
+    CU(cudaEventRecord(ev[1], ctx->s_main));
+    DevFaults f = dev_faults(ctx);
+    uint32_t launches = 2 + (uint32_t)ctx->designs.size();
+    // per-thread scratch, waves sized to a fixed memory budget
+    const size_t budget = (size_t)8 << 30;
+    DBuf<uint64_t> fval, regv;
+    DBuf<uint32_t> stamp, qst, heap, regr;
+    for (size_t d = 0; d < ctx->designs.size(); ++d) {
+        Design &D = *ctx->designs[d];
+        const uint32_t Fd = ctx->f_first[d + 1] - ctx->f_first[d];
+        if (!Fd) continue;
+        const size_t per = (size_t)D.n_net * 12 + (size_t)std::max<uint32_t>(D.N, 1) * 8 + (size_t)std::max<uint32_t>(D.R, 1) * 24;
+        uint32_t wave = (uint32_t)std::max<size_t>(1, std::min<size_t>(Fd, budget / per));
+        const uint32_t sn = D.n_net, snode = std::max<uint32_t>(D.N, 1), sreg = std::max<uint32_t>(D.R, 1);
+        CU(fval.reserve((size_t)wave * sn));
+        CU(stamp.reserve((size_t)wave * sn));
+        CU(qst.reserve((size_t)wave * snode));
+        CU(heap.reserve((size_t)wave * snode));
+        CU(regr.reserve((size_t)wave * 2 * sreg));
+        CU(regv.reserve((size_t)wave * 2 * sreg));
+        for (uint32_t first = 0; first < Fd; first += wave) {
+            const uint32_t cnt = std::min(wave, Fd - first);
+            CU(cudaMemsetAsync(stamp.p, 0, (size_t)cnt * sn * 4, ctx->s_main));
+            CU(cudaMemsetAsync(qst.p, 0, (size_t)cnt * snode * 4, ctx->s_main));
+            CU(launch_plain(ctx->d_designs.p, (uint32_t)d, f, ctx->f_first[d] + first, cnt, fval.p,
+                            stamp.p, qst.p, heap.p, regr.p, regv.p, sn, snode, sreg, ctx->s_main));
+            ++launches;
+        }
+    }
+    CU(cudaEventRecord(ev[4], ctx->s_main));
+    const uint32_t F = ctx->F;
+    if (F) {
+        CU(cudaMemcpyAsync(ctx->p_cycle, ctx->d_cycle.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_port, ctx->d_port.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
+    }
+    CU(cudaEventRecord(ev[5], ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));
+    for (Design *D : ctx->designs) D->trace_valid = true;
+    rtlfs_stats &st = ctx->stats;
+    st = rtlfs_stats{};
+    st.total_ms = ev_ms(ev[0], ev[5]);
+    st.good_ms = ev_ms(ev[0], ev[1]);
+    st.faulty_ms = ev_ms(ev[1], ev[4]);
+    st.n_launches = launches;
+    for (size_t d = 0; d < ctx->designs.size(); ++d) {
+        const Design &D = *ctx->designs[d];
+        for (uint32_t i = ctx->f_first[d]; i < ctx->f_first[d + 1]; ++i) {
+            const uint32_t k = i - ctx->f_first[d];
+            if (out[d]) {
+                out[d][k].detected = ctx->p_det[i];
+                out[d][k].cycle = ctx->p_cycle[i];
+                out[d][k].port = ctx->p_port[i];
+                out[d][k].reserved[0] = out[d][k].reserved[1] = out[d][k].reserved[2] = 0;
+            }
+            st.node_evals += ctx->p_load[i];
+            st.fault_cycles += ctx->p_det[i] == 1 ? (uint64_t)ctx->p_cycle[i] + 1 : D.T;
+        }
+    }
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+int rtlfs_get_stats(const rtlfs_ctx *ctx, rtlfs_stats *out) {
+    if (!ctx || !out) return RTLFS_E_ARG;
+    *out = ctx->stats;
+    return RTLFS_OK;
+}
+
+int rtlfs_good_outputs(rtlfs_ctx *ctx, uint32_t design_id, uint64_t *out) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size() || !out) return fail(ctx, RTLFS_E_ARG, "bad design id or null out");
+    Design &D = *ctx->designs[design_id];
+    if (!D.has_stim) return fail(ctx, RTLFS_E_STATE, "design has no stimulus");
+    CU(cudaSetDevice(ctx->device));
+    if (!D.trace_valid) {
+        int rc = run_good_only(ctx);
+        if (rc != RTLFS_OK) return rc;
+    }
+    std::vector<uint64_t> col(D.T);
+    for (uint32_t o = 0; o < D.O; ++o) {
+        CU(cudaMemcpy(col.data(), D.d_gcol.p + (size_t)D.out_net[o] * D.T, (size_t)D.T * 8, cudaMemcpyDeviceToHost));
+        for (uint32_t t = 0; t < D.T; ++t) out[(size_t)t * D.O + o] = col[t];
+    }
+    return RTLFS_OK;
+}
+
+int rtlfs_good_trace(rtlfs_ctx *ctx, uint32_t design_id, uint64_t *out) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size() || !out) return fail(ctx, RTLFS_E_ARG, "bad design id or null out");
+    Design &D = *ctx->designs[design_id];
+    if (!D.has_stim) return fail(ctx, RTLFS_E_STATE, "design has no stimulus");
+    CU(cudaSetDevice(ctx->device));
+    if (!D.trace_valid) {
+        int rc = run_good_only(ctx);
+        if (rc != RTLFS_OK) return rc;
+    }
+    std::vector<uint64_t> all((size_t)D.n_net * D.T);
+    CU(cudaMemcpy(all.data(), D.d_gcol.p, all.size() * 8, cudaMemcpyDeviceToHost));
+    for (uint32_t e = 0; e < D.n_net; ++e) {
+        const uint64_t *col = all.data() + (size_t)D.ext2int[e] * D.T;
+        for (uint32_t t = 0; t < D.T; ++t) out[(size_t)t * D.n_net + e] = col[t];
+    }
+    return RTLFS_OK;
+}
+
+int rtlfs_design_info(const rtlfs_ctx *ctx, uint32_t design_id, uint32_t *n_nets,
+                      uint32_t *n_levels, uint32_t *n_fanout_edges) {
+    if (!ctx || design_id >= ctx->designs.size()) return RTLFS_E_ARG;
+    const Design &D = *ctx->designs[design_id];
+    if (n_nets) *n_nets = D.n_net;
+    if (n_levels) *n_levels = D.n_levels;
+    if (n_fanout_edges) *n_fanout_edges = D.n_fo;
+    return RTLFS_OK;
+}
+
+}  // extern "C"

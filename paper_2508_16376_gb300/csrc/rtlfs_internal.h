@@ -1,0 +1,117 @@
+// rtlfs_internal.h -- device-side layouts shared by the host code and the kernels.
+//
+// Internal net numbering of a loaded design: [0, I) inputs, [I, I+R) register Qs,
+// [I+R, I+R+N) nodes sorted by topological level (stable within a level), so that
+// every operand of a node has a smaller id and each level is one contiguous id range.
+// The caller's numbering is mapped at load time and restored on output.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rtlfs {
+
+enum : uint32_t {
+    OP_AND = 0, OP_OR, OP_XOR, OP_NOT, OP_ADD, OP_SUB, OP_MUX2, OP_EQ, OP_LT, OP_SHL,
+    OP_SHR, OP_SLICE, OP_CONCAT, OP_CONST
+};
+
+constexpr uint32_t NO_PORT = 0xFFFFFFFFu;
+
+// Node descriptor, 16 bytes: x/y/z = operand net ids (CONST: y:x = value), w = meta.
+// meta bits: [0,4) op, [8,15) width 1..64, [16,24) k = shift amount, slice offset or
+// width(b) for CONCAT, clamped to 64.
+__host__ __device__ inline uint32_t meta_op(uint32_t m) { return m & 15u; }
+__host__ __device__ inline uint32_t meta_w(uint32_t m) { return (m >> 8) & 127u; }
+__host__ __device__ inline uint32_t meta_k(uint32_t m) { return (m >> 16) & 255u; }
+__host__ __device__ inline uint32_t make_meta(uint32_t op, uint32_t w, uint32_t k) {
+    return (op & 15u) | ((w & 127u) << 8) | ((k > 64u ? 64u : k) << 16);
+}
+
+struct DevDesign {
+    uint32_t I, R, N, O, n_net, n_levels, T, n_fo;
+    const uint4    *desc;       // [N]
+    const uint32_t *lvl_start;  // [n_levels + 1] node-index range of each level
+    const uint16_t *node_level; // [N]
+    const uint8_t  *net_w;      // [n_net]
+    const uint32_t *fo_off;     // [n_net + 1] fan-out CSR: consumer node indices
+    const uint32_t *fo_idx;     // [n_fo]
+    const uint32_t *dreg_off;   // [n_net + 1] registers latching each net
+    const uint32_t *dreg_idx;   // [n_dreg]
+    const uint32_t *reg_d;      // [R] internal id of each register's D net
+    const uint32_t *outport;    // [n_net] lowest output port observing the net, or NO_PORT
+    const uint32_t *out_net;    // [O] internal id observed by each port
+    const uint64_t *stim;       // [T][I]
+    uint64_t *rows;             // [T][n_net] good trace, one row per cycle
+    uint64_t *gcol;             // [n_net][T] good trace, one column per net
+};
+
+// All faults of all designs, concatenated in design order.
+struct DevFaults {
+    uint32_t F;
+    const uint32_t *site;       // internal net id
+    const uint8_t  *bit;
+    const uint8_t  *val;
+    const uint16_t *design;     // design index of each fault
+    int32_t  *res_cycle;
+    int32_t  *res_port;
+    uint8_t  *res_det;
+    uint64_t *load;             // node evaluations, summed over simulated cycles
+};
+
+// Light-lane capacities (per fault, per cycle): register diffs, net diffs, pending nodes.
+constexpr int LIGHT_KR = 4;
+constexpr int LIGHT_KD = 12;
+constexpr int LIGHT_KH = 12;
+
+// A fault handed from the light kernel (or the scheduler) to the heavy kernel: resume at
+// cycle t with `nreg` register diffs (reg index, faulty Q value).
+struct HeavyItem {
+    uint32_t fault;
+    uint32_t t;
+    uint32_t nreg;
+    uint32_t reg_r[LIGHT_KR];
+    uint64_t reg_v[LIGHT_KR];
+};
+
+struct Queues {
+    const uint32_t *light_order;   // [n_light] global fault ids, in schedule order
+    uint32_t n_light;
+    unsigned long long *light_head;
+    HeavyItem *heavy_items;        // [cap]
+    uint32_t  *heavy_count;        // device counter of heavy items
+    unsigned long long *heavy_head;
+    uint32_t heavy_cap;
+    unsigned long long *budget_hit; // faults whose work budget ran out
+    uint64_t fault_budget;
+};
+
+// Per-slot scratch of the heavy kernel (one slot per resident CTA).
+struct HeavyScratch {
+    uint64_t *fval;      // [slots][max_net]
+    uint32_t *stamp;     // [slots][max_net]
+    uint32_t *epoch;     // [slots]
+    uint32_t *reg_r;     // [slots][2][max_reg]
+    uint64_t *reg_v;     // [slots][2][max_reg]
+    uint32_t max_net, max_reg, max_node, max_levels;
+};
+
+// Launchers (rtlfs_kernels.cu). All enqueue on `stream` and return the launch status.
+cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
+                              uint32_t n_list, uint32_t max_net, uint32_t max_reg,
+                              bool use_smem, cudaStream_t stream);
+cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,
+                             cudaStream_t stream);
+cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int block,
+                         int grid, cudaStream_t stream);
+cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
+                         int block, int grid, cudaStream_t stream);
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels);
+cudaError_t launch_plain(const DevDesign *d_designs, uint32_t design, DevFaults f,
+                         uint32_t first, uint32_t count, uint64_t *fval, uint32_t *stamp,
+                         uint32_t *qstamp, uint32_t *heap, uint32_t *reg_r, uint64_t *reg_v,
+                         uint32_t stride_net, uint32_t stride_node, uint32_t stride_reg,
+                         cudaStream_t stream);
+int light_max_blocks_per_sm(int block);
+int heavy_max_blocks_per_sm(int block, size_t smem);
+
+}  // namespace rtlfs

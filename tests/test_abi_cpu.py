@@ -1,0 +1,71 @@
+"""CPU-side checks of the C-ABI boundary: the library builds, loads, and exports every
+entry point declared in include/*.h; the binding's struct layouts match the header's
+stated sizes. No compute call is made (there may be no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+
+from paper_2508_16376_gb300 import build, rtlfs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(rtlfs_[a-z_0-9]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    names = _declared()
+    assert "rtlfs_run" in names and "rtlfs_load_design" in names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    # every declared entry point has a binding with the same name
+    assert names <= set(rtlfs.EXPORTS) | {n for n in names if n.startswith("rtlfs_x")}
+
+
+def test_struct_sizes_match_header():
+    assert rtlfs.NODE_DTYPE.itemsize == 24
+    assert rtlfs.REG_DTYPE.itemsize == 8
+    assert rtlfs.FAULT_DTYPE.itemsize == 8
+    assert rtlfs.RESULT_DTYPE.itemsize == 12
+    assert ctypes.sizeof(rtlfs.rtlfs_run_opts) == 4 * 6 + 8 + 32
+    assert ctypes.sizeof(rtlfs.rtlfs_stats) == 6 * 8 + 4 * 8 + 4 + 28
+
+
+def test_create_without_device_fails_cleanly():
+    """With no usable GPU, rtlfs_create returns an error status instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        return
+    lib = rtlfs.load_library()
+    h = ctypes.c_void_p()
+    rc = lib.rtlfs_create(ctypes.byref(h), 0)
+    assert rc != rtlfs.RTLFS_OK and not h.value
+
+
+def test_binding_raises_without_library(tmp_path):
+    try:
+        rtlfs.load_library(str(tmp_path / "missing.so"))
+    except RuntimeError as e:
+        assert "not built" in str(e)
+    else:
+        raise AssertionError("expected a loud failure")
+
+
+def test_design_arrays_roundtrip():
+    from paper_2508_16376_gb300 import synth
+    d = synth.tiny_design(1)
+    nodes, regs, iw, outs = rtlfs.design_arrays(d)
+    assert np.array_equal(nodes["a"], d.node_a) and np.array_equal(regs["d_net"], d.reg_d)
+    assert len(iw) == d.n_in and len(outs) == d.n_out
