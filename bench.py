@@ -241,7 +241,8 @@ def main():
             "wall_ms_per_step": 1000 * wall / args.steps,
             "campaign": {k: last[k] for k in ("good_ms", "prep_ms", "light_ms", "heavy_ms",
                                                "promoted", "heavy_initial", "node_evals",
-                                               "fault_cycles")},
+                                               "fault_cycles", "light_evals", "heavy_evals",
+                                               "light_fault_cycles", "heavy_fault_cycles")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(last["n_launches"]) * args.steps,
@@ -255,7 +256,7 @@ def main():
                                   "unit": UNIT, "ms_per_step": pst["total_ms"],
                                   "wall_s": time.perf_counter() - t1}
     from paper_2508_16376_gb300 import roofline
-    line["roofline"] = roofline.light_kernel_roofline(last, peaks, d)
+    line["roofline"] = roofline.dominant_roofline(last, peaks, d, stim.shape[0])
     sim.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(d, stim, faults)

@@ -115,7 +115,9 @@ typedef struct {
                                 heavy kernel from cycle 0; < 0 = auto */
     int32_t  use_graph;      /* 1 = capture the launch sequence in a CUDA graph and replay */
     uint64_t fault_budget;   /* max node evaluations per fault, 0 = unlimited */
-    uint32_t reserved[8];
+    int32_t  light_cap;      /* light-lane capacity variant: 1 = 4 register diffs / 12 net
+                                diffs / 12 pending nodes, 2 = 8/24/24, 3 = 8/48/48; 0 = auto */
+    uint32_t reserved[7];
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */
@@ -131,7 +133,11 @@ typedef struct {
     uint64_t promoted;       /* light faults promoted to the heavy kernel */
     uint64_t heavy_initial;  /* faults assigned to the heavy kernel from cycle 0 */
     uint32_t n_launches;     /* kernels launched by the run */
-    uint32_t reserved[7];
+    uint32_t reserved;
+    uint64_t light_evals;         /* node evaluations done by the light kernel */
+    uint64_t light_fault_cycles;  /* fault-cycles completed by the light kernel */
+    uint64_t heavy_evals;         /* node evaluations done by the heavy kernel */
+    uint64_t heavy_fault_cycles;  /* fault-cycles completed by the heavy kernel */
 } rtlfs_stats;
 
 typedef struct rtlfs_ctx rtlfs_ctx;   /* opaque */
@@ -199,6 +205,52 @@ int rtlfs_good_trace(rtlfs_ctx *ctx, uint32_t design_id, uint64_t *out);
 /* Design sizes after load: n_nets, number of topological levels, total fan-out edges. */
 int rtlfs_design_info(const rtlfs_ctx *ctx, uint32_t design_id, uint32_t *n_nets,
                       uint32_t *n_levels, uint32_t *n_fanout_edges);
+
+/* ---- load predictor ---------------------------------------------------------------------
+ * The paper balances load with a runtime monitor that marks a node heavy when its share of
+ * the run time passes a threshold (Sec. IV-C-2, Sec. V-A). Here a small MLP predicts each
+ * fault's propagation load (node evaluations summed over the cycles it is simulated,
+ * natural log of 1 + load) before the faulty kernels start; the prediction orders the work
+ * queue and picks the faults that start in the heavy kernel (RTLFS_SCHED_MLP). It never
+ * changes a result.
+ *
+ * Features (5 floats per fault, row-major [n][5]): static fan-out cone size (log2 of the
+ * reconvergence-counting cone estimate, / 20, at most 1.5), topological level of the site
+ * (0 for inputs/registers, else (level+1)/n_levels), register depth from the site to the
+ * nearest output (min(depth,16)/16; 1 if no output is reachable), width of the site net
+ * / 64, and the good-trace toggle rate of the site bit (changes between consecutive
+ * cycles / (T-1)).
+ *
+ * Network: 5 -> 64 (ReLU) -> 64 (ReLU) -> 1, RTLFS_MLP_PARAMS parameters laid out as
+ * W1[5][64], b1[64], W2[64][64], b2[64], w3[64], b3 (W[i][j] connects unit i of one layer
+ * to unit j of the next). Parameters are BF16 (raw uint16 bit patterns); arithmetic
+ * accumulates in FP32 on the CUDA cores. */
+#define RTLFS_MLP_PARAMS 4609
+
+/* Features of every fault of design_id into out[n_faults][5] (runs the good trace first if
+ * needed). Errors: RTLFS_E_ARG, RTLFS_E_STATE, RTLFS_E_CUDA. */
+int rtlfs_features(rtlfs_ctx *ctx, uint32_t design_id, float *out);
+
+/* Load parameters w[RTLFS_MLP_PARAMS] (BF16 bit patterns); resets the optimizer state. */
+int rtlfs_mlp_set_weights(rtlfs_ctx *ctx, const uint16_t *w);
+
+/* Current parameters (BF16 bit patterns) into w[RTLFS_MLP_PARAMS]. RTLFS_E_STATE if none. */
+int rtlfs_mlp_get_weights(rtlfs_ctx *ctx, uint16_t *w);
+
+/* Predictions y[n] for features X[n][5]. RTLFS_E_STATE if no weights are loaded. */
+int rtlfs_mlp_forward(rtlfs_ctx *ctx, const float *X, uint32_t n, float *y);
+
+/* Mean squared error over n samples (*loss) and its gradient grad[RTLFS_MLP_PARAMS]
+ * (FP32) with respect to every parameter, at the current BF16 parameters. */
+int rtlfs_mlp_grad(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, float *loss,
+                   float *grad);
+
+/* Adam training (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on n samples in the
+ * given order, `batch` samples per step, for `epochs` passes; FP32 master parameters,
+ * BF16 copies used by the forward pass. *final_loss (may be null) = mean squared error
+ * accumulated over the last pass. */
+int rtlfs_mlp_train(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, uint32_t epochs,
+                    uint32_t batch, float lr, float *final_loss);
 
 #ifdef __cplusplus
 }

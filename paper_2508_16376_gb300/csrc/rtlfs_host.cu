@@ -7,6 +7,10 @@
 // two streams, results back to the caller.
 #include "../../include/rtlfs.h"
 #include "rtlfs_internal.h"
+#include "rtlfs_sched.h"
+
+#include <cuda_bf16.h>
+#include <deque>
 
 #include <algorithm>
 #include <cmath>
@@ -59,11 +63,17 @@ struct Design {
     std::vector<uint16_t> node_level;
     std::vector<uint8_t> net_w;
     std::vector<uint32_t> fo_off, fo_idx, dreg_off, dreg_idx, reg_d, outport, out_net;
+    std::vector<uint4> netinfo;
+    std::vector<uint2> chunks;
     std::vector<float> cone;          // static fan-out cone size estimate per net (log2 scale)
-    DBuf<uint4> d_desc;
+    std::vector<float> net_static;    // [n_net][4] cone, level, register depth, width (scaled)
+    DBuf<float> d_net_static;
+    DBuf<uint4> d_desc, d_netinfo;
+    DBuf<uint2> d_chunks;
     DBuf<uint32_t> d_lvl_start, d_fo_off, d_fo_idx, d_dreg_off, d_dreg_idx, d_reg_d, d_outport,
         d_out_net;
-    DBuf<uint16_t> d_node_level;
+    DBuf<uint16_t> d_node_level, d_fo_lvl;
+    std::vector<uint16_t> fo_lvl;
     DBuf<uint8_t> d_net_w;
     // stimulus and faults
     uint32_t T = 0;
@@ -98,11 +108,21 @@ struct rtlfs_ctx {
     DBuf<uint32_t> d_order;
     DBuf<HeavyItem> d_init_items, d_prom_items;
     DBuf<uint32_t> d_counters;        // [0] init count, [1] prom count
-    DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget
+    DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget,
+                                      // [4..5] light evals/cycles, [6..7] heavy evals/cycles
     DBuf<uint64_t> h_fval;
-    DBuf<uint32_t> h_stamp, h_epoch, h_regr;
+    DBuf<uint32_t> h_regr;
     DBuf<uint64_t> h_regv;
     uint32_t heavy_slots = 0, heavy_grid = 0, hs_net = 0, hs_reg = 0, hs_node = 0, hs_lv = 0;
+    // scheduler state
+    DBuf<const float *> d_static_ptrs;
+    DBuf<float> d_X, d_heur, d_pred, d_mm;
+    DBuf<uint32_t> d_hist;
+    // load predictor: BF16 weights for inference, FP32 master + Adam moments for training
+    bool has_weights = false;
+    int adam_step = 0;
+    DBuf<__nv_bfloat16> d_wb;
+    DBuf<float> d_master, d_m, d_v, d_grad, d_loss, d_tx, d_ty;
     // pinned host staging of results
     int32_t *p_cycle = nullptr, *p_port = nullptr;
     uint8_t *p_det = nullptr;
@@ -176,6 +196,7 @@ int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
     }
     for (uint32_t o = 0; o < O; ++o)
         if (outs[o] >= n_net) return fail(ctx, RTLFS_E_ARG, "output %u net out of range", o);
+    if (O >= NI_NO_PORT) return fail(ctx, RTLFS_E_ARG, "too many output ports");
 
     // Levelize (Kahn over node->node operand edges); level 0 = no node operand.
     std::vector<uint32_t> indeg(N, 0), ucnt(N + 1, 0);
@@ -209,18 +230,23 @@ int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
     if (N == 0) NL = 0;
     if (NL > 65535) return fail(ctx, RTLFS_E_ARG, "more than 65535 levels");
 
-    // Renumber: nodes sorted by (level, index).
+    // Renumber: nodes sorted by (level, op, index). Grouping a level's nodes by op keeps
+    // the 32 nodes a warp evaluates together on one branch of the op switch.
     D.I = I; D.R = R; D.N = N; D.O = O; D.n_net = n_net; D.n_levels = NL;
     D.lvl_start.assign(NL + 1, 0);
     for (uint32_t n = 0; n < N; ++n) ++D.lvl_start[level[n] + 1];
     for (uint32_t l = 0; l < NL; ++l) D.lvl_start[l + 1] += D.lvl_start[l];
-    std::vector<uint32_t> pos(D.lvl_start.begin(), D.lvl_start.end());
+    std::vector<uint32_t> perm(N);
+    for (uint32_t n = 0; n < N; ++n) perm[n] = n;
+    std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) {
+        return level[a] != level[b] ? level[a] < level[b] : nodes[a].op < nodes[b].op;
+    });
     D.ext2int.resize(n_net);
     D.int2ext.resize(n_net);
     for (uint32_t i = 0; i < IR; ++i) D.ext2int[i] = D.int2ext[i] = i;
     D.node_level.resize(N);
-    for (uint32_t n = 0; n < N; ++n) {
-        const uint32_t k = pos[level[n]]++;
+    for (uint32_t k = 0; k < N; ++k) {
+        const uint32_t n = perm[k];
         D.ext2int[IR + n] = IR + k;
         D.int2ext[IR + k] = IR + n;
         D.node_level[k] = (uint16_t)level[n];
@@ -277,6 +303,8 @@ int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
             }
         }
     }
+    D.fo_lvl.resize(D.n_fo);
+    for (uint32_t e = 0; e < D.n_fo; ++e) D.fo_lvl[e] = D.node_level[D.fo_idx[e]];
     // Latch map: registers whose D is each net.
     D.reg_d.resize(R);
     D.dreg_off.assign(n_net + 1, 0);
@@ -298,6 +326,21 @@ int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
         D.out_net[o] = net;
         D.outport[net] = std::min(D.outport[net], o);
     }
+    // Per-net records and good-trace chunks.
+    D.netinfo.resize(n_net);
+    for (uint32_t e = 0; e < n_net; ++e) {
+        const uint32_t nr = D.dreg_off[e + 1] - D.dreg_off[e];
+        const uint32_t port = D.outport[e] == NO_PORT ? NI_NO_PORT : D.outport[e];
+        D.netinfo[e] = make_uint4(D.fo_off[e], D.fo_off[e + 1], D.dreg_off[e],
+                                  (std::min<uint32_t>(nr, 255u) << 24) | port);
+    }
+    D.chunks.clear();
+    for (uint32_t l = 0; l < NL; ++l) {
+        for (uint32_t lo = D.lvl_start[l]; lo < D.lvl_start[l + 1]; lo += GOOD_BLOCK) {
+            const uint32_t hi = std::min(lo + GOOD_BLOCK, D.lvl_start[l + 1]);
+            D.chunks.push_back(make_uint2(lo, hi | (hi == D.lvl_start[l + 1] ? 0x80000000u : 0u)));
+        }
+    }
     // Static fan-out cone estimate (reverse topological sum, capped): scheduling feature.
     D.cone.assign(n_net, 0.f);
     {
@@ -315,16 +358,51 @@ int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
         }
         for (uint32_t e = 0; e < n_net; ++e) D.cone[e] = (float)std::log2(cs[e]);
     }
+    // Register depth to the outputs: fewest register stages on any path from the net to
+    // an output port (0-1 breadth-first search backwards from the outputs).
+    std::vector<uint32_t> depth(n_net, 0xFFFFFFFFu);
+    {
+        std::deque<uint32_t> dq;
+        for (uint32_t o = 0; o < O; ++o)
+            if (depth[D.out_net[o]] != 0) { depth[D.out_net[o]] = 0; dq.push_front(D.out_net[o]); }
+        while (!dq.empty()) {
+            const uint32_t y = dq.front();
+            dq.pop_front();
+            const uint32_t dy = depth[y];
+            if (y >= IR) {
+                const uint4 d = D.desc[y - IR];
+                const int no = n_ops(meta_op(d.w));
+                const uint32_t ops[3] = {d.x, d.y, d.z};
+                for (int k = 0; k < no; ++k)
+                    if (depth[ops[k]] > dy) { depth[ops[k]] = dy; dq.push_front(ops[k]); }
+            } else if (y >= I) {
+                const uint32_t x = D.reg_d[y - I];
+                if (depth[x] > dy + 1) { depth[x] = dy + 1; dq.push_back(x); }
+            }
+        }
+    }
+    D.net_static.resize((size_t)n_net * 4);
+    for (uint32_t e = 0; e < n_net; ++e) {
+        float *ns = &D.net_static[(size_t)e * 4];
+        ns[0] = std::min(D.cone[e] / 20.f, 1.5f);
+        ns[1] = e < IR ? 0.f : (float)(D.node_level[e - IR] + 1) / (float)std::max<uint32_t>(NL, 1);
+        ns[2] = (float)std::min<uint32_t>(depth[e], 16u) / 16.f;
+        ns[3] = (float)D.net_w[e] / 64.f;
+    }
     return RTLFS_OK;
 }
 
 int upload_design(rtlfs_ctx *ctx, Design &D) {
     CU(D.d_desc.upload(D.desc));
+    CU(D.d_netinfo.upload(D.netinfo));
+    CU(D.d_net_static.upload(D.net_static));
+    CU(D.d_chunks.upload(D.chunks));
     CU(D.d_lvl_start.upload(D.lvl_start));
     CU(D.d_node_level.upload(D.node_level));
     CU(D.d_net_w.upload(D.net_w));
     CU(D.d_fo_off.upload(D.fo_off));
     CU(D.d_fo_idx.upload(D.fo_idx));
+    CU(D.d_fo_lvl.upload(D.fo_lvl));
     CU(D.d_dreg_off.upload(D.dreg_off));
     CU(D.d_dreg_idx.upload(D.dreg_idx));
     CU(D.d_reg_d.upload(D.reg_d));
@@ -337,8 +415,10 @@ DevDesign dev_view(const Design &D) {
     DevDesign v{};
     v.I = D.I; v.R = D.R; v.N = D.N; v.O = D.O; v.n_net = D.n_net; v.n_levels = D.n_levels;
     v.T = D.T; v.n_fo = D.n_fo;
+    v.n_chunks = (uint32_t)D.chunks.size();
+    v.netinfo = D.d_netinfo.p; v.chunks = D.d_chunks.p;
     v.desc = D.d_desc.p; v.lvl_start = D.d_lvl_start.p; v.node_level = D.d_node_level.p;
-    v.net_w = D.d_net_w.p; v.fo_off = D.d_fo_off.p; v.fo_idx = D.d_fo_idx.p;
+    v.net_w = D.d_net_w.p; v.fo_off = D.d_fo_off.p; v.fo_idx = D.d_fo_idx.p; v.fo_lvl = D.d_fo_lvl.p;
     v.dreg_off = D.d_dreg_off.p; v.dreg_idx = D.d_dreg_idx.p; v.reg_d = D.d_reg_d.p;
     v.outport = D.d_outport.p; v.out_net = D.d_out_net.p; v.stim = D.d_stim.p;
     v.rows = D.d_rows.p; v.gcol = D.d_gcol.p;
@@ -351,29 +431,33 @@ constexpr size_t SMEM_LIMIT = 200 * 1024;   // good-trace values in shared memor
 int enqueue_good(rtlfs_ctx *ctx) {
     std::vector<DevDesign> tab;
     std::vector<uint32_t> l_smem, l_glob;
-    uint32_t max_net_s = 0, max_reg_s = 0;
+    uint32_t max_net_s = 0, max_reg_s = 0, max_ch_s = 0, max_ch_g = 0;
     for (size_t i = 0; i < ctx->designs.size(); ++i) {
         Design &D = *ctx->designs[i];
         const size_t cells = (size_t)D.n_net * D.T;
         CU(D.d_rows.reserve(cells));
         CU(D.d_gcol.reserve(cells));
         tab.push_back(dev_view(D));
-        const size_t smem = ((size_t)D.n_net + D.R) * sizeof(uint64_t);
+        const uint32_t nch = (uint32_t)D.chunks.size();
+        const size_t smem = ((size_t)D.n_net + D.R) * sizeof(uint64_t) + (size_t)nch * sizeof(uint2);
         if (smem <= SMEM_LIMIT) {
             l_smem.push_back((uint32_t)i);
             max_net_s = std::max(max_net_s, D.n_net);
             max_reg_s = std::max(max_reg_s, D.R);
+            max_ch_s = std::max(max_ch_s, nch);
         } else {
             l_glob.push_back((uint32_t)i);
+            max_ch_g = std::max(max_ch_g, nch);
         }
     }
     CU(ctx->d_designs.upload(tab));
     CU(ctx->d_list_smem.upload(l_smem));
     CU(ctx->d_list_glob.upload(l_glob));
+    if (max_ch_g * sizeof(uint2) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
     CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, (uint32_t)l_smem.size(), max_net_s,
-                         max_reg_s, true, ctx->s_main));
+                         max_reg_s, max_ch_s, true, ctx->s_main));
     CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, (uint32_t)l_glob.size(), 0, 0,
-                         false, ctx->s_main));
+                         max_ch_g, false, ctx->s_main));
     for (Design *D : ctx->designs)
         CU(launch_transpose(D->d_gcol.p, D->d_rows.p, D->n_net, D->T, ctx->s_main));
     return RTLFS_OK;
@@ -434,7 +518,7 @@ int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots) {
         mn = std::max(mn, D->n_net); mr = std::max(mr, D->R);
         mnode = std::max(mnode, D->N); ml = std::max(ml, D->n_levels);
     }
-    const size_t smem = heavy_smem_bytes(mnode, ml);
+    const size_t smem = heavy_smem_bytes(mnode, ml, mn);
     if (smem > 220 * 1024) return fail(ctx, RTLFS_E_ARG, "design too large for the heavy kernel bitmap");
     int per_sm = heavy_max_blocks_per_sm(block, smem);
     if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "heavy kernel cannot be resident with block %d", block);
@@ -442,15 +526,10 @@ int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots) {
     slots = std::min(slots, per_sm * ctx->n_sm);
     const bool grow = slots > (int)ctx->heavy_slots || mn > ctx->hs_net || mr > ctx->hs_reg;
     if (grow) {
-        ctx->h_fval.release(); ctx->h_stamp.release(); ctx->h_epoch.release();
-        ctx->h_regr.release(); ctx->h_regv.release();
+        ctx->h_fval.release(); ctx->h_regr.release(); ctx->h_regv.release();
         CU(ctx->h_fval.reserve((size_t)slots * mn));
-        CU(ctx->h_stamp.reserve((size_t)slots * mn));
-        CU(ctx->h_epoch.reserve(slots));
         CU(ctx->h_regr.reserve((size_t)slots * 2 * mr));
         CU(ctx->h_regv.reserve((size_t)slots * 2 * mr));
-        CU(cudaMemset(ctx->h_stamp.p, 0, (size_t)slots * mn * sizeof(uint32_t)));
-        CU(cudaMemset(ctx->h_epoch.p, 0, (size_t)slots * sizeof(uint32_t)));
         ctx->heavy_slots = slots; ctx->hs_net = mn; ctx->hs_reg = mr;
     }
     ctx->hs_node = mnode; ctx->hs_lv = ml;
@@ -460,11 +539,34 @@ int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots) {
 
 HeavyScratch heavy_view(rtlfs_ctx *ctx) {
     HeavyScratch s{};
-    s.fval = ctx->h_fval.p; s.stamp = ctx->h_stamp.p; s.epoch = ctx->h_epoch.p;
+    s.fval = ctx->h_fval.p;
     s.reg_r = ctx->h_regr.p; s.reg_v = ctx->h_regv.p;
     s.max_net = ctx->hs_net; s.max_reg = ctx->hs_reg; s.max_node = ctx->hs_node;
     s.max_levels = ctx->hs_lv;
     return s;
+}
+
+int ensure_sched_buffers(rtlfs_ctx *ctx) {
+    std::vector<const float *> ptrs;
+    for (Design *D : ctx->designs) ptrs.push_back(D->d_net_static.p);
+    CU(ctx->d_static_ptrs.upload(ptrs));
+    const size_t F = std::max<size_t>(ctx->F, 1);
+    CU(ctx->d_X.reserve(F * MLP_IN));
+    CU(ctx->d_heur.reserve(F));
+    CU(ctx->d_pred.reserve(F));
+    CU(ctx->d_mm.reserve(2));
+    CU(ctx->d_hist.reserve(SORT_BUCKETS));
+    return RTLFS_OK;
+}
+
+int ensure_mlp(rtlfs_ctx *ctx) {
+    CU(ctx->d_wb.reserve(MLP_PARAMS));
+    CU(ctx->d_master.reserve(MLP_PARAMS));
+    CU(ctx->d_m.reserve(MLP_PARAMS));
+    CU(ctx->d_v.reserve(MLP_PARAMS));
+    CU(ctx->d_grad.reserve(MLP_PARAMS));
+    CU(ctx->d_loss.reserve(1));
+    return RTLFS_OK;
 }
 
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
@@ -496,7 +598,7 @@ int rtlfs_create(rtlfs_ctx **out, int device) {
         CU(cudaStreamCreateWithFlags(&ctx->s_heavy, cudaStreamNonBlocking));
         for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
         CU(ctx->d_counters.reserve(4));
-        CU(ctx->d_heads.reserve(4));
+        CU(ctx->d_heads.reserve(8));
         return RTLFS_OK;
     };
     rc = init();
@@ -604,7 +706,9 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     o.heavy_frac = -1.f;
     if (opts_in) o = *opts_in;
     const int lblock = o.light_block > 0 ? o.light_block : 128;
-    const int hblock = o.heavy_block > 0 ? o.heavy_block : 128;
+    const int lcap = o.light_cap > 0 ? o.light_cap - 1 : 1;
+    if (lcap > 2) return fail(ctx, RTLFS_E_ARG, "light_cap must be 0..3");
+    const int hblock = o.heavy_block > 0 ? o.heavy_block : 32;
     if (lblock < 32 || lblock > 256 || (lblock & 31)) return fail(ctx, RTLFS_E_ARG, "light_block must be a multiple of 32 in 32..256");
     if (hblock < 32 || hblock > 1024 || (hblock & 31)) return fail(ctx, RTLFS_E_ARG, "heavy_block must be a multiple of 32 in 32..1024");
     CU(cudaSetDevice(ctx->device));
@@ -613,30 +717,23 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     if (rc != RTLFS_OK) return rc;
     const uint32_t F = ctx->F;
 
-    // Schedule: queue order and heavy pre-assignment (host side).
-    std::vector<uint32_t> order(F);
-    for (uint32_t i = 0; i < F; ++i) order[i] = i;
-    std::vector<HeavyItem> init;
-    if (o.scheduler != RTLFS_SCHED_PLAIN && F) {
-        std::vector<float> score(F);
-        for (size_t d = 0; d < ctx->designs.size(); ++d) {
-            Design &D = *ctx->designs[d];
-            for (uint32_t i = ctx->f_first[d]; i < ctx->f_first[d + 1]; ++i)
-                score[i] = D.cone[D.f_site[i - ctx->f_first[d]]];
-        }
-        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return score[a] > score[b]; });
-        const float hf = o.heavy_frac >= 0.f ? std::min(o.heavy_frac, 1.f) : 0.0f;
-        const uint32_t nh = (uint32_t)(hf * F);
-        for (uint32_t i = 0; i < nh; ++i) {
-            HeavyItem h{};
-            h.fault = order[i];
-            init.push_back(h);
-        }
-        order.erase(order.begin(), order.begin() + nh);
+    // Schedule. PLAIN: fault-list order, nothing pre-assigned to the heavy kernel (order
+    // uploaded from the host). HEURISTIC / MLP: computed on the device after the good
+    // trace -- features, score (static cone x toggle rate, or the predictor), bucket sort
+    // by descending score; the top heavy_frac of the faults start in the heavy kernel.
+    const bool dev_sched = o.scheduler != RTLFS_SCHED_PLAIN && F > 0;
+    const bool use_mlp = o.scheduler == RTLFS_SCHED_MLP && ctx->has_weights;
+    const float hf = dev_sched ? (o.heavy_frac >= 0.f ? std::min(o.heavy_frac, 1.f) : 0.0f) : 0.f;
+    const uint32_t n_heavy = (uint32_t)(hf * F);
+    if (!dev_sched) {
+        std::vector<uint32_t> order(F);
+        for (uint32_t i = 0; i < F; ++i) order[i] = i;
+        CU(ctx->d_order.upload(order));
+    } else {
+        rc = ensure_sched_buffers(ctx);
+        if (rc != RTLFS_OK) return rc;
     }
-    CU(ctx->d_order.upload(order));
-    if (!init.empty()) CU(cudaMemcpy(ctx->d_init_items.p, init.data(), init.size() * sizeof(HeavyItem), cudaMemcpyHostToDevice));
-    const uint32_t counters[4] = {(uint32_t)init.size(), 0u, 0u, 0u};
+    const uint32_t counters[4] = {n_heavy, 0u, 0u, 0u};
     CU(cudaMemcpy(ctx->d_counters.p, counters, sizeof(counters), cudaMemcpyHostToDevice));
     rc = ensure_heavy_scratch(ctx, hblock, o.heavy_ctas);
     if (rc != RTLFS_OK) return rc;
@@ -644,8 +741,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
 
     DevFaults f = dev_faults(ctx);
     Queues ql{};
-    ql.light_order = ctx->d_order.p;
-    ql.n_light = (uint32_t)order.size();
+    ql.light_order = ctx->d_order.p + n_heavy;
+    ql.n_light = F - n_heavy;
     ql.light_head = ctx->d_heads.p + 0;
     ql.heavy_items = ctx->d_prom_items.p;
     ql.heavy_count = ctx->d_counters.p + 1;
@@ -653,31 +750,47 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     ql.heavy_cap = F;
     ql.budget_hit = ctx->d_heads.p + 3;
     ql.fault_budget = o.fault_budget;
+    ql.counters = ctx->d_heads.p + 4;
     Queues qi = ql;
     qi.heavy_items = ctx->d_init_items.p;
     qi.heavy_count = ctx->d_counters.p + 0;
     qi.heavy_head = ctx->d_heads.p + 1;
+    qi.counters = ctx->d_heads.p + 6;
     Queues qp = ql;
+    qp.counters = ctx->d_heads.p + 6;
 
     cudaEvent_t *ev = ctx->ev;
     CU(cudaEventRecord(ev[0], ctx->s_main));
-    CU(cudaMemsetAsync(ctx->d_heads.p, 0, 4 * sizeof(unsigned long long), ctx->s_main));
+    CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
     if (F) CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
     uint32_t launches = 0;
     rc = enqueue_good(ctx);
     if (rc != RTLFS_OK) return rc;
     launches += 2 + (uint32_t)ctx->designs.size();
     CU(cudaEventRecord(ev[1], ctx->s_main));
-    const int per_sm = light_max_blocks_per_sm(lblock);
+    if (dev_sched) {
+        CU(launch_features(ctx->d_designs.p, f, ctx->d_static_ptrs.p, ctx->d_X.p, ctx->d_heur.p, ctx->s_main));
+        const float *score = ctx->d_heur.p;
+        if (use_mlp) {
+            CU(launch_mlp_forward(ctx->d_wb.p, ctx->d_X.p, F, ctx->d_pred.p, ctx->s_main));
+            score = ctx->d_pred.p;
+            ++launches;
+        }
+        CU(launch_order(score, F, ctx->d_mm.p, ctx->d_hist.p, ctx->d_order.p, n_heavy,
+                        ctx->d_init_items.p, ctx->s_main));
+        launches += 6 + (n_heavy ? 1 : 0);
+    }
+    CU(cudaEventRecord(ev[6], ctx->s_main));
+    const int per_sm = light_max_blocks_per_sm(lcap, lblock);
     if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "light kernel cannot be resident");
     const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((ql.n_light + lblock - 1) / lblock,
                                                                    (int64_t)per_sm * ctx->n_sm));
     const int hgrid = (int)ctx->heavy_grid;
     HeavyScratch hs = heavy_view(ctx);
-    if (ql.n_light) { CU(launch_light(ctx->d_designs.p, f, ql, lblock, lgrid, ctx->s_main)); ++launches; }
+    if (ql.n_light) { CU(launch_light(ctx->d_designs.p, f, ql, lcap, lblock, lgrid, ctx->s_main)); ++launches; }
     CU(cudaEventRecord(ev[2], ctx->s_main));
-    CU(cudaStreamWaitEvent(ctx->s_heavy, ev[1], 0));
-    if (!init.empty()) { CU(launch_heavy(ctx->d_designs.p, f, qi, hs, hblock, hgrid, ctx->s_heavy)); ++launches; }
+    CU(cudaStreamWaitEvent(ctx->s_heavy, ev[6], 0));
+    if (n_heavy) { CU(launch_heavy(ctx->d_designs.p, f, qi, hs, hblock, hgrid, ctx->s_heavy)); ++launches; }
     CU(cudaStreamWaitEvent(ctx->s_heavy, ev[2], 0));
     CU(cudaEventRecord(ev[3], ctx->s_heavy));
     CU(launch_heavy(ctx->d_designs.p, f, qp, hs, hblock, hgrid, ctx->s_heavy));
@@ -690,7 +803,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
         CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
     }
-    unsigned long long heads[4] = {0, 0, 0, 0};
+    unsigned long long heads[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t cnts[4] = {0, 0, 0, 0};
     CU(cudaMemcpyAsync(heads, ctx->d_heads.p, sizeof(heads), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaMemcpyAsync(cnts, ctx->d_counters.p, sizeof(cnts), cudaMemcpyDeviceToHost, ctx->s_main));
@@ -703,13 +816,17 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     st = rtlfs_stats{};
     st.total_ms = ev_ms(ev[0], ev[5]);
     st.good_ms = ev_ms(ev[0], ev[1]);
-    st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
-    st.faulty_ms = ev_ms(ev[1], ev[4]);
-    st.light_ms = ev_ms(ev[1], ev[2]);
+    st.prep_ms = ev_ms(ev[1], ev[6]) + std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
+    st.faulty_ms = ev_ms(ev[6], ev[4]);
+    st.light_ms = ev_ms(ev[6], ev[2]);
     st.heavy_ms = ev_ms(ev[3], ev[4]);
     st.promoted = cnts[1];
     st.heavy_initial = cnts[0];
     st.n_launches = launches;
+    st.light_evals = heads[4];
+    st.light_fault_cycles = heads[5];
+    st.heavy_evals = heads[6];
+    st.heavy_fault_cycles = heads[7];
     for (size_t d = 0; d < ctx->designs.size(); ++d) {
         const Design &D = *ctx->designs[d];
         rtlfs_result *r = out[d];
@@ -851,6 +968,126 @@ int rtlfs_good_trace(rtlfs_ctx *ctx, uint32_t design_id, uint64_t *out) {
         const uint64_t *col = all.data() + (size_t)D.ext2int[e] * D.T;
         for (uint32_t t = 0; t < D.T; ++t) out[(size_t)t * D.n_net + e] = col[t];
     }
+    return RTLFS_OK;
+}
+
+int rtlfs_features(rtlfs_ctx *ctx, uint32_t design_id, float *out) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size() || !out) return fail(ctx, RTLFS_E_ARG, "bad design id or null out");
+    CU(cudaSetDevice(ctx->device));
+    int rc = build_faults(ctx);
+    if (rc != RTLFS_OK) return rc;
+    for (Design *D : ctx->designs)
+        if (!D->trace_valid) { rc = run_good_only(ctx); if (rc != RTLFS_OK) return rc; break; }
+    if (!ctx->F) return RTLFS_OK;
+    rc = ensure_sched_buffers(ctx);
+    if (rc != RTLFS_OK) return rc;
+    CU(launch_features(ctx->d_designs.p, dev_faults(ctx), ctx->d_static_ptrs.p, ctx->d_X.p,
+                       ctx->d_heur.p, ctx->s_main));
+    const uint32_t a = ctx->f_first[design_id], b = ctx->f_first[design_id + 1];
+    CU(cudaMemcpyAsync(out, ctx->d_X.p + (size_t)a * MLP_IN, (size_t)(b - a) * MLP_IN * sizeof(float),
+                       cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));
+    return RTLFS_OK;
+}
+
+int rtlfs_mlp_set_weights(rtlfs_ctx *ctx, const uint16_t *w) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!w) return fail(ctx, RTLFS_E_ARG, "null weights");
+    CU(cudaSetDevice(ctx->device));
+    int rc = ensure_mlp(ctx);
+    if (rc != RTLFS_OK) return rc;
+    std::vector<float> master(MLP_PARAMS);
+    for (int i = 0; i < MLP_PARAMS; ++i) {
+        const uint32_t bits = (uint32_t)w[i] << 16;
+        std::memcpy(&master[i], &bits, 4);
+    }
+    CU(cudaMemcpy(ctx->d_wb.p, w, MLP_PARAMS * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->d_master.p, master.data(), MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
+    CU(cudaMemset(ctx->d_m.p, 0, MLP_PARAMS * sizeof(float)));
+    CU(cudaMemset(ctx->d_v.p, 0, MLP_PARAMS * sizeof(float)));
+    CU(cudaMemset(ctx->d_grad.p, 0, MLP_PARAMS * sizeof(float)));
+    ctx->adam_step = 0;
+    ctx->has_weights = true;
+    return RTLFS_OK;
+}
+
+int rtlfs_mlp_get_weights(rtlfs_ctx *ctx, uint16_t *w) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!w) return fail(ctx, RTLFS_E_ARG, "null weights");
+    if (!ctx->has_weights) return fail(ctx, RTLFS_E_STATE, "no weights loaded");
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaMemcpy(w, ctx->d_wb.p, MLP_PARAMS * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    return RTLFS_OK;
+}
+
+static int upload_samples(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n) {
+    CU(ctx->d_tx.reserve((size_t)n * MLP_IN));
+    CU(cudaMemcpy(ctx->d_tx.p, X, (size_t)n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice));
+    if (t) {
+        CU(ctx->d_ty.reserve(n));
+        CU(cudaMemcpy(ctx->d_ty.p, t, (size_t)n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return RTLFS_OK;
+}
+
+int rtlfs_mlp_forward(rtlfs_ctx *ctx, const float *X, uint32_t n, float *y) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!ctx->has_weights) return fail(ctx, RTLFS_E_STATE, "no weights loaded");
+    if (n && (!X || !y)) return fail(ctx, RTLFS_E_ARG, "null array");
+    if (!n) return RTLFS_OK;
+    CU(cudaSetDevice(ctx->device));
+    int rc = upload_samples(ctx, X, nullptr, n);
+    if (rc != RTLFS_OK) return rc;
+    CU(ctx->d_pred.reserve(n));
+    CU(launch_mlp_forward(ctx->d_wb.p, ctx->d_tx.p, n, ctx->d_pred.p, ctx->s_main));
+    CU(cudaMemcpyAsync(y, ctx->d_pred.p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));
+    return RTLFS_OK;
+}
+
+int rtlfs_mlp_grad(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, float *loss,
+                   float *grad) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!ctx->has_weights) return fail(ctx, RTLFS_E_STATE, "no weights loaded");
+    if (!n || !X || !t || !loss || !grad) return fail(ctx, RTLFS_E_ARG, "null array or n = 0");
+    CU(cudaSetDevice(ctx->device));
+    int rc = upload_samples(ctx, X, t, n);
+    if (rc != RTLFS_OK) return rc;
+    CU(cudaMemsetAsync(ctx->d_grad.p, 0, MLP_PARAMS * sizeof(float), ctx->s_main));
+    CU(cudaMemsetAsync(ctx->d_loss.p, 0, sizeof(float), ctx->s_main));
+    CU(launch_mlp_grad(ctx->d_wb.p, ctx->d_tx.p, ctx->d_ty.p, n, ctx->d_grad.p, ctx->d_loss.p, ctx->s_main));
+    float lsum = 0.f;
+    CU(cudaMemcpyAsync(grad, ctx->d_grad.p, MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaMemcpyAsync(&lsum, ctx->d_loss.p, sizeof(float), cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));
+    CU(cudaMemsetAsync(ctx->d_grad.p, 0, MLP_PARAMS * sizeof(float), ctx->s_main));
+    *loss = lsum / (float)n;
+    return RTLFS_OK;
+}
+
+int rtlfs_mlp_train(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, uint32_t epochs,
+                    uint32_t batch, float lr, float *final_loss) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!ctx->has_weights) return fail(ctx, RTLFS_E_STATE, "no weights loaded");
+    if (!n || !X || !t || !batch || !(lr > 0.f)) return fail(ctx, RTLFS_E_ARG, "bad training arguments");
+    CU(cudaSetDevice(ctx->device));
+    int rc = upload_samples(ctx, X, t, n);
+    if (rc != RTLFS_OK) return rc;
+    float lsum = 0.f;
+    for (uint32_t ep = 0; ep < epochs; ++ep) {
+        CU(cudaMemsetAsync(ctx->d_loss.p, 0, sizeof(float), ctx->s_main));
+        for (uint32_t s0 = 0; s0 < n; s0 += batch) {
+            const uint32_t nb = std::min(batch, n - s0);
+            CU(launch_mlp_grad(ctx->d_wb.p, ctx->d_tx.p + (size_t)s0 * MLP_IN, ctx->d_ty.p + s0, nb,
+                               ctx->d_grad.p, ctx->d_loss.p, ctx->s_main));
+            CU(launch_mlp_adam(ctx->d_master.p, ctx->d_wb.p, ctx->d_grad.p, ctx->d_m.p, ctx->d_v.p, lr,
+                               0.9f, 0.999f, 1e-8f, ++ctx->adam_step, ctx->s_main));
+        }
+    }
+    CU(cudaMemcpyAsync(&lsum, ctx->d_loss.p, sizeof(float), cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));
+    if (final_loss) *final_loss = lsum / (float)n;
     return RTLFS_OK;
 }
 

@@ -17,6 +17,9 @@ enum : uint32_t {
 
 constexpr uint32_t NO_PORT = 0xFFFFFFFFu;
 
+// Threads of the good-trace CTA = maximum nodes per good-trace chunk.
+constexpr uint32_t GOOD_BLOCK = 512;
+
 // Node descriptor, 16 bytes: x/y/z = operand net ids (CONST: y:x = value), w = meta.
 // meta bits: [0,4) op, [8,15) width 1..64, [16,24) k = shift amount, slice offset or
 // width(b) for CONCAT, clamped to 64.
@@ -27,14 +30,25 @@ __host__ __device__ inline uint32_t make_meta(uint32_t op, uint32_t w, uint32_t 
     return (op & 15u) | ((w & 127u) << 8) | ((k > 64u ? 64u : k) << 16);
 }
 
+// Per-net record, 16 bytes: x = first fan-out entry, y = end of fan-out entries,
+// z = first latch entry (dreg_idx), w = (latch count, 255 = read dreg_off) << 24 | port,
+// port = lowest output port observing the net (0xFFFFFF = none).
+constexpr uint32_t NI_NO_PORT = 0xFFFFFFu;
+__host__ __device__ inline uint32_t ni_port(uint32_t w) { return w & 0xFFFFFFu; }
+__host__ __device__ inline uint32_t ni_nreg(uint32_t w) { return w >> 24; }
+
 struct DevDesign {
     uint32_t I, R, N, O, n_net, n_levels, T, n_fo;
+    uint32_t n_chunks;          // good-trace chunks (<= GOOD_BLOCK nodes each, never across levels)
+    const uint4    *netinfo;    // [n_net]
+    const uint2    *chunks;     // [n_chunks] {first node, end node | 1<<31 if last of its level}
     const uint4    *desc;       // [N]
     const uint32_t *lvl_start;  // [n_levels + 1] node-index range of each level
     const uint16_t *node_level; // [N]
     const uint8_t  *net_w;      // [n_net]
     const uint32_t *fo_off;     // [n_net + 1] fan-out CSR: consumer node indices
     const uint32_t *fo_idx;     // [n_fo]
+    const uint16_t *fo_lvl;     // [n_fo] level of each consumer
     const uint32_t *dreg_off;   // [n_net + 1] registers latching each net
     const uint32_t *dreg_idx;   // [n_dreg]
     const uint32_t *reg_d;      // [R] internal id of each register's D net
@@ -59,9 +73,9 @@ struct DevFaults {
 };
 
 // Light-lane capacities (per fault, per cycle): register diffs, net diffs, pending nodes.
-constexpr int LIGHT_KR = 4;
-constexpr int LIGHT_KD = 12;
-constexpr int LIGHT_KH = 12;
+// Three compiled variants, chosen per run (rtlfs_run_opts.light_cap 1..3).
+constexpr int LIGHT_KR = 8;    // upper bound of every variant's register-diff capacity
+constexpr int LIGHT_CAPS[3][3] = {{4, 12, 12}, {8, 24, 24}, {8, 48, 48}};
 
 // A fault handed from the light kernel (or the scheduler) to the heavy kernel: resume at
 // cycle t with `nreg` register diffs (reg index, faulty Q value).
@@ -83,13 +97,19 @@ struct Queues {
     uint32_t heavy_cap;
     unsigned long long *budget_hit; // faults whose work budget ran out
     uint64_t fault_budget;
+    unsigned long long *counters;   // [0] node evaluations, [1] fault-cycles simulated
 };
+
+// Words of the heavy kernel's net bitmap remembered for clearing; beyond this many the
+// whole bitmap is cleared at the end of the cycle.
+constexpr uint32_t HEAVY_DLIST = 512;
+// Fan-out ranges a heavy CTA collects per level before marking consumers together; a
+// range beyond this many is marked by the thread that kept the net.
+constexpr uint32_t HEAVY_FRANGE = 256;
 
 // Per-slot scratch of the heavy kernel (one slot per resident CTA).
 struct HeavyScratch {
-    uint64_t *fval;      // [slots][max_net]
-    uint32_t *stamp;     // [slots][max_net]
-    uint32_t *epoch;     // [slots]
+    uint64_t *fval;      // [slots][max_net] faulty values of the nets that differ
     uint32_t *reg_r;     // [slots][2][max_reg]
     uint64_t *reg_v;     // [slots][2][max_reg]
     uint32_t max_net, max_reg, max_node, max_levels;
@@ -98,20 +118,20 @@ struct HeavyScratch {
 // Launchers (rtlfs_kernels.cu). All enqueue on `stream` and return the launch status.
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              bool use_smem, cudaStream_t stream);
+                              uint32_t max_chunks, bool use_smem, cudaStream_t stream);
 cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,
                              cudaStream_t stream);
-cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int block,
+cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int cap, int block,
                          int grid, cudaStream_t stream);
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream);
-size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels);
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net);
 cudaError_t launch_plain(const DevDesign *d_designs, uint32_t design, DevFaults f,
                          uint32_t first, uint32_t count, uint64_t *fval, uint32_t *stamp,
                          uint32_t *qstamp, uint32_t *heap, uint32_t *reg_r, uint64_t *reg_v,
                          uint32_t stride_net, uint32_t stride_node, uint32_t stride_reg,
                          cudaStream_t stream);
-int light_max_blocks_per_sm(int block);
+int light_max_blocks_per_sm(int cap, int block);
 int heavy_max_blocks_per_sm(int block, size_t smem);
 
 }  // namespace rtlfs

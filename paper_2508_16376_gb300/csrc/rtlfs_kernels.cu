@@ -63,24 +63,53 @@ __device__ __forceinline__ uint64_t force_bit(uint64_t x, uint64_t bm, bool sv) 
 // ===================================================================================
 // Good-machine trace. One CTA per design walks the cycles; inside a cycle the nodes of
 // one topological level are independent and are spread over the threads, with a
-// barrier between levels. Net values of the current cycle live in shared memory when
+// barrier between levels. The node list is cut into chunks of at most GOOD_BLOCK nodes that
+// never straddle a level, so every thread owns at most one node per chunk and the same
+// node in every cycle; each thread keeps the descriptors of its next three chunks in
+// registers (a prefetch ring that wraps into the next cycle), so descriptor loads are
+// off the critical path. Net values of the current cycle live in shared memory when
 // they fit (USE_SMEM) and are streamed to the row-major trace rows[t][net].
 // ===================================================================================
 template <bool USE_SMEM>
 __global__ void __launch_bounds__(1024)
 good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
-                  uint32_t max_net) {
+                  uint32_t max_net, uint32_t max_reg, uint32_t max_chunks) {
     extern __shared__ uint64_t gsm[];
     const DevDesign &D = designs[list[blockIdx.x]];
-    const uint32_t I = D.I, R = D.R, IR = I + R, n_net = D.n_net, T = D.T, NL = D.n_levels;
+    const uint32_t I = D.I, R = D.R, IR = I + R, n_net = D.n_net, T = D.T, NC = D.n_chunks;
     const uint32_t tid = threadIdx.x, B = blockDim.x;
-    uint64_t *val = gsm;                 // [max_net] when USE_SMEM
-    uint64_t *qn = gsm + max_net;        // [max_reg] next register values when USE_SMEM
+    uint64_t *val = gsm;                                     // [max_net] when USE_SMEM
+    uint64_t *qn = gsm + (USE_SMEM ? max_net : 0);           // [max_reg] when USE_SMEM
+    uint2 *ch = reinterpret_cast<uint2 *>(gsm + (USE_SMEM ? (size_t)max_net + max_reg : 0));
+    for (uint32_t c = tid; c < NC; c += B) ch[c] = D.chunks[c];
+    // this thread's input and its first two registers, kept in registers for every cycle
+    const uint64_t in_mask = tid < I ? wmask(D.net_w[tid]) : 0ull;
+    const uint32_t r0 = tid, r1 = tid + B;
+    const uint32_t rd0 = r0 < R ? D.reg_d[r0] : 0, rd1 = r1 < R ? D.reg_d[r1] : 0;
+    const uint64_t rm0 = r0 < R ? wmask(D.net_w[I + r0]) : 0, rm1 = r1 < R ? wmask(D.net_w[I + r1]) : 0;
+    __syncthreads();
+
+    auto fetch = [&](uint32_t c) -> uint4 {
+        const uint2 b = ch[c];
+        const uint32_t n = b.x + tid;
+        return n < (b.y & 0x7FFFFFFFu) ? __ldg(D.desc + n) : make_uint4(0, 0, 0, 0xFFFFFFFFu);
+    };
+    uint4 d0 = make_uint4(0, 0, 0, 0xFFFFFFFFu), d1 = d0, d2 = d0;
+    uint32_t cf = 0;                 // next chunk to prefetch (wraps)
+    if (NC) {
+        d0 = fetch(cf); cf = cf + 1 == NC ? 0 : cf + 1;
+        d1 = fetch(cf); cf = cf + 1 == NC ? 0 : cf + 1;
+        d2 = fetch(cf); cf = cf + 1 == NC ? 0 : cf + 1;
+    }
+    uint64_t s_next = (tid < I) ? __ldg(D.stim + tid) : 0ull;
+
     for (uint32_t t = 0; t < T; ++t) {
         uint64_t *row = D.rows + (size_t)t * n_net;
+        const uint64_t s_cur = s_next;
+        if (tid < I && t + 1 < T) s_next = __ldg(D.stim + (size_t)(t + 1) * I + tid);
         for (uint32_t i = tid; i < IR; i += B) {
             uint64_t v;
-            if (i < I) v = D.stim[(size_t)t * I + i] & wmask(D.net_w[i]);
+            if (i < I) v = (i == tid ? s_cur : __ldg(D.stim + (size_t)t * I + i)) & (i == tid ? in_mask : wmask(D.net_w[i]));
             else if (t == 0) v = 0ull;
             else if (USE_SMEM) v = qn[i - I];
             else v = (row - n_net)[D.reg_d[i - I]] & wmask(D.net_w[i]);   // previous row
@@ -88,24 +117,30 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
             row[i] = v;
         }
         __syncthreads();
-        for (uint32_t L = 0; L < NL; ++L) {
-            const uint32_t lo = D.lvl_start[L], hi = D.lvl_start[L + 1];
-            for (uint32_t n = lo + tid; n < hi; n += B) {
-                const uint4 d = D.desc[n];
-                const uint32_t op = meta_op(d.w);
+        for (uint32_t c = 0; c < NC; ++c) {
+            const uint2 b = ch[c];
+            if (d0.w != 0xFFFFFFFFu) {
+                const uint32_t n = b.x + tid;
+                const uint32_t op = meta_op(d0.w);
                 const int no = n_operands(op);
-                uint64_t a = 0, b = 0, c = 0;
-                if (no >= 1) a = USE_SMEM ? val[d.x] : row[d.x];
-                if (no >= 2) b = USE_SMEM ? val[d.y] : row[d.y];
-                if (no >= 3) c = USE_SMEM ? val[d.z] : row[d.z];
-                const uint64_t v = eval_op(d, a, b, c);
+                uint64_t a = 0, bb = 0, cc = 0;
+                if (no >= 1) a = USE_SMEM ? val[d0.x] : row[d0.x];
+                if (no >= 2) bb = USE_SMEM ? val[d0.y] : row[d0.y];
+                if (no >= 3) cc = USE_SMEM ? val[d0.z] : row[d0.z];
+                const uint64_t v = eval_op(d0, a, bb, cc);
                 if (USE_SMEM) val[IR + n] = v;
                 row[IR + n] = v;
             }
-            __syncthreads();
+            if (b.y & 0x80000000u) __syncthreads();
+            d0 = d1;
+            d1 = d2;
+            d2 = fetch(cf);
+            cf = cf + 1 == NC ? 0 : cf + 1;
         }
         if (USE_SMEM) {
-            for (uint32_t r = tid; r < R; r += B) qn[r] = val[D.reg_d[r]] & wmask(D.net_w[I + r]);
+            if (r0 < R) qn[r0] = val[rd0] & rm0;
+            if (r1 < R) qn[r1] = val[rd1] & rm1;
+            for (uint32_t r = tid + 2 * B; r < R; r += B) qn[r] = val[D.reg_d[r]] & wmask(D.net_w[I + r]);
         }
         __syncthreads();
     }
@@ -147,7 +182,7 @@ __global__ void transpose_kernel(uint64_t *__restrict__ gcol, const uint64_t *__
 // the fault, with its start-of-cycle state, to the heavy kernel.
 // ===================================================================================
 template <int KR, int KD, int KH>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
     extern __shared__ __align__(16) unsigned char lsm[];
     const uint32_t B = blockDim.x, tx = threadIdx.x;
@@ -169,6 +204,9 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
         const DevDesign &D = designs[f.design[fid]];
         const uint32_t I = D.I, IR = D.I + D.R, T = D.T;
         const uint64_t *__restrict__ gcol = D.gcol;
+        const uint4 *__restrict__ netinfo = D.netinfo;
+        const uint4 *__restrict__ desc = D.desc;
+        const uint32_t *__restrict__ fo_idx = D.fo_idx;
         const uint32_t site = f.site[fid];
         const uint32_t bit = f.bit[fid];
         const bool sv = f.val[fid] != 0;
@@ -184,15 +222,24 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
         for (;;) {
             if (nreg == 0) {
                 // Skip quiescent cycles: nothing differs unless the site bit is activated.
-                while (t < T) {
-                    const uint64_t g = __ldg(scol + t);
-                    if (((g >> bit) & 1ull) != (uint64_t)sv) break;
-                    ++t;
+                // Four cycles per step, loads issued together.
+                const uint64_t want = sv ? 0ull : bm;   // good bit value that is not activated
+                while (t + 4 <= T) {
+                    const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
+                    const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
+                    if ((g0 & bm) != want) break;
+                    if ((g1 & bm) != want) { t += 1; break; }
+                    if ((g2 & bm) != want) { t += 2; break; }
+                    if ((g3 & bm) != want) { t += 3; break; }
+                    t += 4;
+                }
+                if (t + 4 > T) {
+                    while (t < T && (__ldg(scol + t) & bm) == want) ++t;
                 }
                 if (t >= T) break;
             }
             const uint32_t nb = cur ^ 1u;
-            uint32_t nd = 0, nh = 0, nreg_new = 0, minport = NO_PORT;
+            uint32_t nd = 0, nh = 0, nreg_new = 0, minport = NI_NO_PORT;
             uint64_t filter = 0;
             bool ovf = false;
             const uint64_t load_at_cycle_start = load;   // the heavy kernel redoes a promoted cycle
@@ -228,26 +275,40 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
                 if (nh > 0) HP(i) = x;
                 return top;
             };
-            auto add_diff = [&](uint32_t net, uint64_t v, uint64_t g) {
+            // Keep net (faulty v, good g, record ni): diff entry, detection, fan-out, latch.
+            auto add_diff = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
                 if (nd >= (uint32_t)KD) { ovf = true; return; }
                 DN(nd) = net;
                 DV(nd) = v;
                 ++nd;
                 filter |= 1ull << (net & 63u);
-                const uint32_t p = __ldg(D.outport + net);
+                const uint32_t p = ni_port(ni.w);
                 minport = p < minport ? p : minport;
-                const uint32_t e1 = __ldg(D.fo_off + net + 1);
-                for (uint32_t e = __ldg(D.fo_off + net); e < e1; ++e) heap_push(__ldg(D.fo_idx + e));
-                const uint32_t r1 = __ldg(D.dreg_off + net + 1);
-                for (uint32_t e = __ldg(D.dreg_off + net); e < r1; ++e) {
-                    const uint32_t r = __ldg(D.dreg_idx + e);
-                    const uint64_t wm = wmask(__ldg(D.net_w + I + r));
-                    const uint64_t qv = v & wm;
-                    if (qv != (g & wm)) {
-                        if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
-                        RR(nb, nreg_new) = r;
-                        RV(nb, nreg_new) = qv;
-                        ++nreg_new;
+                if (ni.y - ni.x > (uint32_t)KH) { ovf = true; return; }
+                for (uint32_t e = ni.x; e < ni.y; e += 4) {
+                    // four independent loads in flight, then the pushes
+                    const uint32_t c0 = __ldg(fo_idx + e);
+                    const uint32_t c1 = e + 1 < ni.y ? __ldg(fo_idx + e + 1) : 0xFFFFFFFFu;
+                    const uint32_t c2 = e + 2 < ni.y ? __ldg(fo_idx + e + 2) : 0xFFFFFFFFu;
+                    const uint32_t c3 = e + 3 < ni.y ? __ldg(fo_idx + e + 3) : 0xFFFFFFFFu;
+                    heap_push(c0);
+                    if (c1 != 0xFFFFFFFFu) heap_push(c1);
+                    if (c2 != 0xFFFFFFFFu) heap_push(c2);
+                    if (c3 != 0xFFFFFFFFu) heap_push(c3);
+                }
+                uint32_t nr = ni_nreg(ni.w);
+                if (nr) {
+                    if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                    for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
+                        const uint32_t r = __ldg(D.dreg_idx + e);
+                        const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                        const uint64_t qv = v & wm;
+                        if (qv != (g & wm)) {
+                            if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
+                            RR(nb, nreg_new) = r;
+                            RV(nb, nreg_new) = qv;
+                            ++nreg_new;
+                        }
                     }
                 }
             };
@@ -265,12 +326,12 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
                 uint64_t qv = RV(cur, k);
                 if (net == site) { qv = force_bit(qv, bm, sv); site_seeded = true; }
                 const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (qv != g) add_diff(net, qv, g);
+                if (qv != g) add_diff(net, qv, g, __ldg(netinfo + net));
             }
             if (site < IR && !site_seeded && !ovf) {
                 const uint64_t g = __ldg(scol + t);
                 const uint64_t fv = force_bit(g, bm, sv);
-                if (fv != g) add_diff(site, fv, g);
+                if (fv != g) add_diff(site, fv, g, __ldg(netinfo + site));
             }
             if (site_node != 0xFFFFFFFFu && !ovf) heap_push(site_node);
             uint32_t last = 0xFFFFFFFFu;
@@ -278,7 +339,11 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
                 const uint32_t n = heap_pop();
                 if (n == last) continue;
                 last = n;
-                const uint4 d = __ldg(D.desc + n);
+                const uint32_t net = IR + n;
+                // independent loads first: descriptor, net record, good value
+                const uint4 d = __ldg(desc + n);
+                const uint4 ni = __ldg(netinfo + net);
+                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
                 const uint32_t op = meta_op(d.w);
                 const int no = n_operands(op);
                 uint64_t a = 0, b = 0, c = 0;
@@ -288,9 +353,7 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
                 uint64_t v = eval_op(d, a, b, c);
                 if (n == site_node) v = force_bit(v, bm, sv);
                 ++load;
-                const uint32_t net = IR + n;
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (v != g) add_diff(net, v, g);
+                if (v != g) add_diff(net, v, g, ni);
             }
             if (ovf) {
                 const uint32_t p = atomicAdd(q.heavy_count, 1u);
@@ -308,7 +371,7 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
                 status = 2;
                 break;
             }
-            if (minport != NO_PORT) {
+            if (minport != NI_NO_PORT) {
                 det_cycle = (int32_t)t;
                 det_port = (int32_t)minport;
                 status = 1;
@@ -326,6 +389,9 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
             f.res_port[fid] = det_port;
             if (status == 3) atomicAdd(q.budget_hit, 1ull);
         }
+        // t is the first cycle not completed (detection cycle counts as simulated)
+        atomicAdd(q.counters + 0, (unsigned long long)load);
+        atomicAdd(q.counters + 1, (unsigned long long)(status == 1 ? t + 1 : t));
     }
 #undef RV
 #undef RR
@@ -335,32 +401,37 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
 }
 
 // ===================================================================================
-// Heavy kernel: one CTA per fault. The fault's faulty values live in per-slot scratch
-// (value + cycle stamp per net, so nothing is cleared between cycles); a shared-memory
-// bitmap over the node index space marks the nodes with a differing operand, and a
-// per-level counter lets the CTA skip levels with nothing to do. Levels are processed
-// in order, the dirty nodes of one level in parallel (the bad gates of the fault split
-// over the threads), with one barrier per non-empty level.
+// Heavy kernel: one CTA per fault (by default a single warp). Shared memory holds a bitmap
+// over the nodes (dirty: some operand differs), the number of dirty nodes per level (so an
+// empty level costs one shared read), a bitmap over the nets (differs this cycle) and a
+// list of fan-out ranges to expand. Differing values live in per-slot global scratch.
+// Each level runs in two phases: (1) the dirty nodes of the level are evaluated in
+// parallel -- the fault's bad gates split over the threads -- and every kept net appends
+// its fan-out range; (2) all threads mark the consumers of those ranges together, so a
+// control net with thousands of readers costs a few passes instead of one thread's loop.
 // ===================================================================================
 __global__ void __launch_bounds__(1024)
 heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
-    const uint32_t nwords = (S.max_node + 31) / 32;
-    uint32_t *bm = hsm;                  // [nwords] dirty bits
-    uint32_t *cnt = bm + nwords;         // [max_levels] dirty nodes per level
+    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
+    uint32_t *bm = hsm;                  // [nwn] dirty nodes
+    uint32_t *cnt = bm + nwn;            // [max_levels] dirty nodes per level
+    uint32_t *dbm = cnt + S.max_levels;  // [nwd] nets that differ this cycle
+    uint32_t *dlist = dbm + nwd;         // [HEAVY_DLIST] words of dbm to clear
+    uint2 *frange = reinterpret_cast<uint2 *>(dlist + HEAVY_DLIST);   // [HEAVY_FRANGE]
     __shared__ unsigned long long s_item;
-    __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded;
+    __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
     __shared__ unsigned long long s_load;
     const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
     const uint32_t lane = tid & 31u, warp = tid >> 5;
     uint64_t *fval = S.fval + (size_t)slot * S.max_net;
-    uint32_t *stamp = S.stamp + (size_t)slot * S.max_net;
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
 
-    for (uint32_t i = tid; i < nwords; i += B) bm[i] = 0;
+    for (uint32_t i = tid; i < nwn; i += B) bm[i] = 0;
     for (uint32_t i = tid; i < S.max_levels; i += B) cnt[i] = 0;
-    uint32_t epoch = S.epoch[slot];
+    for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
+    if (tid == 0) s_nfr = 0;
     __syncthreads();
 
     for (;;) {
@@ -374,12 +445,16 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         const DevDesign &D = designs[f.design[fid]];
         const uint32_t I = D.I, IR = D.I + D.R, T = D.T, NL = D.n_levels;
         const uint64_t *__restrict__ gcol = D.gcol;
+        const uint4 *__restrict__ netinfo = D.netinfo;
+        const uint32_t *__restrict__ fo_idx = D.fo_idx;
+        const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
         const uint32_t site = f.site[fid];
         const uint32_t bit = f.bit[fid];
         const bool sv = f.val[fid] != 0;
         const uint64_t bmask = 1ull << bit;
         const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
         uint32_t t = it.t, nreg = it.nreg, cur = 0;
+        const uint32_t t_start = it.t;
         for (uint32_t k = tid; k < nreg; k += B) {
             regR[k] = it.reg_r[k];
             regV[k] = it.reg_v[k];
@@ -387,11 +462,32 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         if (tid == 0) s_load = 0;
         int status = 0;
         int32_t det_cycle = -1, det_port = -1;
-        if (epoch > 0xFFFFF000u) {      // stamps about to wrap: clear and restart
-            for (uint32_t i = tid; i < S.max_net; i += B) stamp[i] = 0;
-            epoch = 0;
-        }
         __syncthreads();
+
+        // Mark the consumers of one fan-out range (all threads of the CTA share the work
+        // when called from expand(); a single thread when the range list is full).
+        auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
+            for (uint32_t e = e0 + first; e < e1; e += step) {
+                const uint32_t c = __ldg(fo_idx + e);
+                const uint32_t lv = __ldg(fo_lvl + e);
+                const uint32_t b1 = 1u << (c & 31u);
+                const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
+                if (!(o2 & b1)) atomicAdd(&cnt[lv], 1u);
+            }
+        };
+        // Ranges live in a ring indexed by a per-cycle append counter s_nfr; fr_begin (the
+        // same in every thread, advanced only after a barrier) is the first unexpanded one.
+        uint32_t fr_begin = 0;
+        // Phase 2: every thread takes a share of every recorded range. Call after a barrier.
+        auto expand = [&]() {
+            const uint32_t end = s_nfr;
+            const uint32_t n = min(end - fr_begin, HEAVY_FRANGE);
+            for (uint32_t r = 0; r < n; ++r) {
+                const uint2 fr = frange[(fr_begin + r) % HEAVY_FRANGE];
+                mark_range(fr.x, fr.y, tid, B);
+            }
+            fr_begin = end;
+        };
 
         for (;;) {
             if (nreg == 0) {
@@ -410,25 +506,30 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                 t = s_t;
                 if (t >= T) break;
             }
-            ++epoch;
             const uint32_t nb = cur ^ 1u;
-            if (tid == 0) { s_nreg_new = 0; s_minport = NO_PORT; s_site_seeded = 0; }
+            if (tid == 0) { s_nreg_new = 0; s_minport = NI_NO_PORT; s_site_seeded = 0; s_nd = 0; s_nfr = 0; }
+            fr_begin = 0;
             __syncthreads();
 
-            auto mark = [&](uint32_t net, uint64_t v, uint64_t g) {
-                stamp[net] = epoch;
+            // Keep a differing net: value, detection, latch, and its fan-out range.
+            auto keep = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
                 fval[net] = v;
-                const uint32_t p = __ldg(D.outport + net);
-                if (p != NO_PORT) atomicMin(&s_minport, p);
-                const uint32_t e1 = __ldg(D.fo_off + net + 1);
-                for (uint32_t e = __ldg(D.fo_off + net); e < e1; ++e) {
-                    const uint32_t c = __ldg(D.fo_idx + e);
-                    const uint32_t b1 = 1u << (c & 31u);
-                    const uint32_t old = atomicOr(&bm[c >> 5], b1);
-                    if (!(old & b1)) atomicAdd(&cnt[__ldg(D.node_level + c)], 1u);
+                const uint32_t wbit = 1u << (net & 31u);
+                const uint32_t old = atomicOr(&dbm[net >> 5], wbit);
+                if (!old) {   // first bit of this word: remember the word for clearing
+                    const uint32_t k = atomicAdd(&s_nd, 1u);
+                    if (k < HEAVY_DLIST) dlist[k] = net >> 5;
                 }
-                const uint32_t r1 = __ldg(D.dreg_off + net + 1);
-                for (uint32_t e = __ldg(D.dreg_off + net); e < r1; ++e) {
+                const uint32_t p = ni_port(ni.w);
+                if (p != NI_NO_PORT) atomicMin(&s_minport, p);
+                if (ni.y > ni.x) {
+                    const uint32_t k = atomicAdd(&s_nfr, 1u);
+                    if (k - fr_begin < HEAVY_FRANGE) frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
+                    else mark_range(ni.x, ni.y, 0, 1);   // ring full: mark here
+                }
+                uint32_t nr = ni_nreg(ni.w);
+                if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
                     const uint32_t r = __ldg(D.dreg_idx + e);
                     const uint64_t wm = wmask(__ldg(D.net_w + I + r));
                     const uint64_t qv = v & wm;
@@ -440,23 +541,24 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                 }
             };
             auto lookup = [&](uint32_t x) -> uint64_t {
-                if (stamp[x] == epoch) return fval[x];
+                if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
                 return __ldg(gcol + (size_t)x * T + t);
             };
 
             for (uint32_t k = tid; k < nreg; k += B) {
                 const uint32_t net = I + regR[cur * S.max_reg + k];
                 uint64_t qv = regV[cur * S.max_reg + k];
-                if (net == site) { qv = force_bit(qv, bmask, sv); s_site_seeded = 1; }
+                const uint4 ni = __ldg(netinfo + net);
                 const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (qv != g) mark(net, qv, g);
+                if (net == site) { qv = force_bit(qv, bmask, sv); s_site_seeded = 1; }
+                if (qv != g) keep(net, qv, g, ni);
             }
             __syncthreads();
             if (tid == 0) {
                 if (site < IR && !s_site_seeded) {
                     const uint64_t g = __ldg(scol + t);
                     const uint64_t fv = force_bit(g, bmask, sv);
-                    if (fv != g) mark(site, fv, g);
+                    if (fv != g) keep(site, fv, g, __ldg(netinfo + site));
                 }
                 if (site >= IR) {
                     const uint32_t c = site - IR;
@@ -465,6 +567,8 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                     if (!(old & b1)) atomicAdd(&cnt[__ldg(D.node_level + c)], 1u);
                 }
             }
+            __syncthreads();
+            expand();
             __syncthreads();
             uint32_t my_load = 0;
             for (uint32_t L = 0; L < NL; ++L) {
@@ -481,27 +585,40 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                         const uint32_t j = __ffs(bits) - 1;
                         bits &= bits - 1;
                         const uint32_t n = (w << 5) + j;
+                        const uint32_t net = IR + n;
+                        // independent loads first: descriptor, net record, good value
                         const uint4 d = __ldg(D.desc + n);
+                        const uint4 ni = __ldg(netinfo + net);
+                        const uint64_t g = __ldg(gcol + (size_t)net * T + t);
                         const uint32_t op = meta_op(d.w);
                         const int no = n_operands(op);
                         uint64_t a = 0, b = 0, c = 0;
                         if (no >= 1) a = lookup(d.x);
                         if (no >= 2) b = lookup(d.y);
                         if (no >= 3) c = lookup(d.z);
-                        const uint32_t net = IR + n;
                         uint64_t v = eval_op(d, a, b, c);
                         if (net == site) v = force_bit(v, bmask, sv);
                         ++my_load;
-                        const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                        if (v != g) mark(net, v, g);
+                        if (v != g) keep(net, v, g, ni);
                     }
                 }
                 __syncthreads();
+                if (s_nfr != fr_begin) {   // uniform: read after the barrier
+                    expand();
+                    __syncthreads();
+                }
                 if (tid == 0) cnt[L] = 0;
             }
             if (my_load) atomicAdd(&s_load, (unsigned long long)my_load);
             __syncthreads();
-            if (s_minport != NO_PORT) {
+            // clear the net bitmap for the next cycle
+            const uint32_t nd = s_nd;
+            if (nd <= HEAVY_DLIST) {
+                for (uint32_t k = tid; k < nd; k += B) dbm[dlist[k]] = 0;
+            } else {
+                for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
+            }
+            if (s_minport != NI_NO_PORT) {
                 det_cycle = (int32_t)t;
                 det_port = (int32_t)s_minport;
                 status = 1;
@@ -520,10 +637,12 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
             f.res_cycle[fid] = det_cycle;
             f.res_port[fid] = det_port;
             if (status == 3) atomicAdd(q.budget_hit, 1ull);
+            atomicAdd(q.counters + 0, (unsigned long long)s_load);
+            const uint32_t t_end = status == 1 ? t + 1 : min(t, T);
+            atomicAdd(q.counters + 1, (unsigned long long)(t_end - t_start));
         }
         __syncthreads();
     }
-    if (tid == 0) S.epoch[slot] = epoch;
 }
 
 // ===================================================================================
@@ -656,20 +775,23 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
 
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              bool use_smem, cudaStream_t stream) {
+                              uint32_t max_chunks, bool use_smem, cudaStream_t stream) {
     if (n_list == 0) return cudaSuccess;
-    const size_t smem = use_smem ? ((size_t)max_net + (size_t)max_reg) * sizeof(uint64_t) : 0;
+    const size_t smem = (use_smem ? ((size_t)max_net + max_reg) * sizeof(uint64_t) : 0) +
+                        (size_t)max_chunks * sizeof(uint2);
     cudaError_t e;
     if (use_smem) {
         e = cudaFuncSetAttribute(good_trace_kernel<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        good_trace_kernel<true><<<n_list, 1024, smem, stream>>>(d_designs, design_list, max_net);
+        good_trace_kernel<true><<<n_list, GOOD_BLOCK, smem, stream>>>(d_designs, design_list, max_net,
+                                                               max_reg, max_chunks);
     } else {
         e = cudaFuncSetAttribute(good_trace_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        good_trace_kernel<false><<<n_list, 1024, smem, stream>>>(d_designs, design_list, max_net);
+        good_trace_kernel<false><<<n_list, GOOD_BLOCK, smem, stream>>>(d_designs, design_list, 0, 0,
+                                                                max_chunks);
     }
     return cudaGetLastError();
 }
@@ -681,33 +803,47 @@ cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_ne
     return cudaGetLastError();
 }
 
-static size_t light_smem(int block) {
-    return (size_t)block * ((2 * LIGHT_KR + LIGHT_KD) * sizeof(uint64_t) +
-                            (2 * LIGHT_KR + LIGHT_KD + LIGHT_KH) * sizeof(uint32_t));
+static size_t light_smem(int cap, int block) {
+    const int KR = LIGHT_CAPS[cap][0], KD = LIGHT_CAPS[cap][1], KH = LIGHT_CAPS[cap][2];
+    return (size_t)block * ((2 * KR + KD) * sizeof(uint64_t) + (2 * KR + KD + KH) * sizeof(uint32_t));
 }
 
-int light_max_blocks_per_sm(int block) {
+template <int C>
+static void *light_fn() {
+    return (void *)light_kernel<LIGHT_CAPS[C][0], LIGHT_CAPS[C][1], LIGHT_CAPS[C][2]>;
+}
+
+static void *light_kernel_ptr(int cap) {
+    return cap == 0 ? light_fn<0>() : cap == 1 ? light_fn<1>() : light_fn<2>();
+}
+
+int light_max_blocks_per_sm(int cap, int block) {
+    if (cap < 0 || cap > 2) return 0;
     int n = 0;
-    const size_t smem = light_smem(block);
-    cudaFuncSetAttribute(light_kernel<LIGHT_KR, LIGHT_KD, LIGHT_KH>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, light_kernel<LIGHT_KR, LIGHT_KD, LIGHT_KH>,
-                                                  block, smem);
+    const size_t smem = light_smem(cap, block);
+    if (smem > 227 * 1024) return 0;
+    void *fn = light_kernel_ptr(cap);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 0;
     return n;
 }
 
-cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int block, int grid,
-                         cudaStream_t stream) {
-    const size_t smem = light_smem(block);
-    cudaError_t e = cudaFuncSetAttribute(light_kernel<LIGHT_KR, LIGHT_KD, LIGHT_KH>,
+cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int cap, int block,
+                         int grid, cudaStream_t stream) {
+    if (cap < 0 || cap > 2) return cudaErrorInvalidValue;
+    const size_t smem = light_smem(cap, block);
+    cudaError_t e = cudaFuncSetAttribute(light_kernel_ptr(cap),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    light_kernel<LIGHT_KR, LIGHT_KD, LIGHT_KH><<<grid, block, smem, stream>>>(d_designs, f, q);
-    return cudaGetLastError();
+    void *args[] = {(void *)&d_designs, (void *)&f, (void *)&q};
+    return cudaLaunchKernel(light_kernel_ptr(cap), dim3(grid), dim3(block), args, smem, stream);
 }
 
-size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels) {
-    return ((size_t)(max_node + 31) / 32 + max_levels) * sizeof(uint32_t);
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net) {
+    size_t words = (size_t)(max_node + 31) / 32 + max_levels + (max_net + 31) / 32 + HEAVY_DLIST;
+    words = (words + 1) & ~(size_t)1;   // 8-byte alignment of the range list
+    return words * sizeof(uint32_t) + HEAVY_FRANGE * sizeof(uint2);
 }
 
 int heavy_max_blocks_per_sm(int block, size_t smem) {
@@ -719,7 +855,7 @@ int heavy_max_blocks_per_sm(int block, size_t smem) {
 
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream) {
-    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels);
+    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net);
     cudaError_t e = cudaFuncSetAttribute(heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -38,7 +38,8 @@ class rtlfs_run_opts(ctypes.Structure):
     _fields_ = [("scheduler", ctypes.c_int32), ("light_block", ctypes.c_int32),
                 ("heavy_block", ctypes.c_int32), ("heavy_ctas", ctypes.c_int32),
                 ("heavy_frac", ctypes.c_float), ("use_graph", ctypes.c_int32),
-                ("fault_budget", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 8)]
+                ("fault_budget", ctypes.c_uint64), ("light_cap", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32 * 7)]
 
 
 class rtlfs_stats(ctypes.Structure):
@@ -47,7 +48,9 @@ class rtlfs_stats(ctypes.Structure):
                 ("light_ms", ctypes.c_double), ("heavy_ms", ctypes.c_double),
                 ("fault_cycles", ctypes.c_uint64), ("node_evals", ctypes.c_uint64),
                 ("promoted", ctypes.c_uint64), ("heavy_initial", ctypes.c_uint64),
-                ("n_launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+                ("n_launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("light_evals", ctypes.c_uint64), ("light_fault_cycles", ctypes.c_uint64),
+                ("heavy_evals", ctypes.c_uint64), ("heavy_fault_cycles", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -75,7 +78,16 @@ EXPORTS = {
     "rtlfs_good_outputs": ([V, ctypes.c_uint32, V], ctypes.c_int),
     "rtlfs_good_trace": ([V, ctypes.c_uint32, V], ctypes.c_int),
     "rtlfs_design_info": ([V, ctypes.c_uint32, V, V, V], ctypes.c_int),
+    "rtlfs_features": ([V, ctypes.c_uint32, V], ctypes.c_int),
+    "rtlfs_mlp_set_weights": ([V, V], ctypes.c_int),
+    "rtlfs_mlp_get_weights": ([V, V], ctypes.c_int),
+    "rtlfs_mlp_forward": ([V, V, ctypes.c_uint32, V], ctypes.c_int),
+    "rtlfs_mlp_grad": ([V, V, V, ctypes.c_uint32, V, V], ctypes.c_int),
+    "rtlfs_mlp_train": ([V, V, V, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                         ctypes.c_float, V], ctypes.c_int),
 }
+MLP_PARAMS = 4609
+MLP_IN = 5
 
 
 def load_library(path: Optional[str] = None):
@@ -230,6 +242,51 @@ def rtlfs_design_info(ctx, design_id: int) -> Tuple[int, int, int]:
     _check(ctx, load_library().rtlfs_design_info(ctx, design_id, ctypes.byref(a),
                                                  ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def rtlfs_features(ctx, design_id: int, n_faults: int) -> np.ndarray:
+    out = np.zeros((n_faults, MLP_IN), np.float32)
+    if n_faults:
+        _check(ctx, load_library().rtlfs_features(ctx, design_id, _ptr(out)))
+    return out
+
+
+def rtlfs_mlp_set_weights(ctx, w_bf16: np.ndarray) -> None:
+    w = np.ascontiguousarray(w_bf16, np.uint16)
+    assert w.size == MLP_PARAMS
+    _check(ctx, load_library().rtlfs_mlp_set_weights(ctx, _ptr(w)))
+
+
+def rtlfs_mlp_get_weights(ctx) -> np.ndarray:
+    w = np.zeros(MLP_PARAMS, np.uint16)
+    _check(ctx, load_library().rtlfs_mlp_get_weights(ctx, _ptr(w)))
+    return w
+
+
+def rtlfs_mlp_forward(ctx, X: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.zeros(X.shape[0], np.float32)
+    _check(ctx, load_library().rtlfs_mlp_forward(ctx, _ptr(X), X.shape[0], _ptr(y)))
+    return y
+
+
+def rtlfs_mlp_grad(ctx, X: np.ndarray, t: np.ndarray):
+    X = np.ascontiguousarray(X, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    g = np.zeros(MLP_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(ctx, load_library().rtlfs_mlp_grad(ctx, _ptr(X), _ptr(t), X.shape[0],
+                                              ctypes.byref(loss), _ptr(g)))
+    return float(loss.value), g
+
+
+def rtlfs_mlp_train(ctx, X: np.ndarray, t: np.ndarray, epochs: int, batch: int, lr: float) -> float:
+    X = np.ascontiguousarray(X, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    loss = ctypes.c_float()
+    _check(ctx, load_library().rtlfs_mlp_train(ctx, _ptr(X), _ptr(t), X.shape[0], epochs, batch,
+                                               lr, ctypes.byref(loss)))
+    return float(loss.value)
 
 
 # ---- convenience wrapper ----------------------------------------------------------------

@@ -40,7 +40,7 @@ def test_struct_sizes_match_header():
     assert rtlfs.FAULT_DTYPE.itemsize == 8
     assert rtlfs.RESULT_DTYPE.itemsize == 12
     assert ctypes.sizeof(rtlfs.rtlfs_run_opts) == 4 * 6 + 8 + 32
-    assert ctypes.sizeof(rtlfs.rtlfs_stats) == 6 * 8 + 4 * 8 + 4 + 28
+    assert ctypes.sizeof(rtlfs.rtlfs_stats) == 6 * 8 + 4 * 8 + 8 + 4 * 8
 
 
 def test_create_without_device_fails_cleanly():
