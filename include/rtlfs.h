@@ -117,7 +117,11 @@ typedef struct {
     uint64_t fault_budget;   /* max node evaluations per fault, 0 = unlimited */
     int32_t  light_cap;      /* light-lane capacity variant: 1 = 4 register diffs / 12 net
                                 diffs / 12 pending nodes, 2 = 8/24/24, 3 = 8/48/48; 0 = auto */
-    uint32_t reserved[7];
+    int32_t  window;         /* cycles per window: every live fault advances through the same
+                                window of cycles, the good trace of the next window, the light
+                                kernel and the heavy kernel overlap on three streams; 0 = each
+                                fault runs its whole timeline in one light/heavy pass */
+    uint32_t reserved[6];
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */

@@ -88,12 +88,33 @@ struct Design {
 
 }  // namespace
 
+struct GoodLaunch {
+    uint32_t n_smem = 0, n_glob = 0, max_net_s = 0, max_reg_s = 0, max_ch_s = 0, max_ch_g = 0;
+};
+
 struct rtlfs_ctx {
     int device = 0;
+    GoodLaunch gl;
+    // CUDA graph of the campaign's launch sequence, replayed while its key matches
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint64_t> graph_key;
+    uint32_t graph_launches = 0;
+    cudaEvent_t ev_graph[2] = {};
+    // pinned scratch: [0..7] queue heads/counters, [8..9] heavy counts, [10..11] counter init
+    unsigned long long *p_small = nullptr;
     int n_sm = 0;
     std::string err;
     std::vector<Design *> designs;
-    cudaStream_t s_main = nullptr, s_heavy = nullptr;
+    cudaStream_t s_main = nullptr, s_heavy = nullptr, s_good = nullptr;
+    // windowed campaign state
+    DBuf<uint8_t> w_st_nreg;
+    DBuf<uint32_t> w_st_r, w_live0, w_live1, w_cnt32, w_pool_r0, w_pool_r1;
+    DBuf<uint64_t> w_st_v, w_pool_v0, w_pool_v1;
+    DBuf<unsigned long long> w_cnt64;
+    DBuf<HeavyCarry> w_carry0, w_carry1;
+    uint64_t w_pool_cap = 0;
+    cudaEvent_t ev_wg = nullptr, ev_wl = nullptr;
+    std::vector<cudaEvent_t> ev_win;   // [4][nw]: light start/end, heavy start/end
     cudaEvent_t ev[8] = {};
     DBuf<DevDesign> d_designs;
     DBuf<uint32_t> d_list_smem, d_list_glob;
@@ -108,6 +129,7 @@ struct rtlfs_ctx {
     DBuf<uint32_t> d_order;
     DBuf<HeavyItem> d_init_items, d_prom_items;
     DBuf<uint32_t> d_counters;        // [0] init count, [1] prom count
+    DBuf<uint32_t> d_err;             // set by a kernel whose bounded wait ran out
     DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget,
                                       // [4..5] light evals/cycles, [6..7] heavy evals/cycles
     DBuf<uint64_t> h_fval;
@@ -425,10 +447,10 @@ DevDesign dev_view(const Design &D) {
     return v;
 }
 
-constexpr size_t SMEM_LIMIT = 200 * 1024;   // good-trace values in shared memory up to this
+constexpr size_t SMEM_LIMIT = 227 * 1024;   // dynamic shared memory of one good-trace CTA
 
-// Allocate traces, upload the design table, enqueue good trace + transposes on s_main.
-int enqueue_good(rtlfs_ctx *ctx) {
+// Allocate traces and upload the design table and good-trace launch lists.
+int prepare_good(rtlfs_ctx *ctx) {
     std::vector<DevDesign> tab;
     std::vector<uint32_t> l_smem, l_glob;
     uint32_t max_net_s = 0, max_reg_s = 0, max_ch_s = 0, max_ch_g = 0;
@@ -439,12 +461,13 @@ int enqueue_good(rtlfs_ctx *ctx) {
         CU(D.d_gcol.reserve(cells));
         tab.push_back(dev_view(D));
         const uint32_t nch = (uint32_t)D.chunks.size();
-        const size_t smem = ((size_t)D.n_net + D.R) * sizeof(uint64_t) + (size_t)nch * sizeof(uint2);
-        if (smem <= SMEM_LIMIT) {
+        // net values in shared memory when the design fits together with the designs
+        // already on the shared-memory list (one launch covers the whole list)
+        const uint32_t mn = std::max(max_net_s, D.n_net), mr = std::max(max_reg_s, D.R);
+        const uint32_t mc = std::max(max_ch_s, nch);
+        if (good_smem_bytes(true, mn, mr, mc) <= SMEM_LIMIT) {
             l_smem.push_back((uint32_t)i);
-            max_net_s = std::max(max_net_s, D.n_net);
-            max_reg_s = std::max(max_reg_s, D.R);
-            max_ch_s = std::max(max_ch_s, nch);
+            max_net_s = mn; max_reg_s = mr; max_ch_s = mc;
         } else {
             l_glob.push_back((uint32_t)i);
             max_ch_g = std::max(max_ch_g, nch);
@@ -453,14 +476,28 @@ int enqueue_good(rtlfs_ctx *ctx) {
     CU(ctx->d_designs.upload(tab));
     CU(ctx->d_list_smem.upload(l_smem));
     CU(ctx->d_list_glob.upload(l_glob));
-    if (max_ch_g * sizeof(uint2) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
-    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, (uint32_t)l_smem.size(), max_net_s,
-                         max_reg_s, max_ch_s, true, ctx->s_main));
-    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, (uint32_t)l_glob.size(), 0, 0,
-                         max_ch_g, false, ctx->s_main));
+    if (good_smem_bytes(false, 0, 0, max_ch_g) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
+    CU(ctx->d_err.reserve(1));
+    ctx->gl = {(uint32_t)l_smem.size(), (uint32_t)l_glob.size(), max_net_s, max_reg_s, max_ch_s, max_ch_g};
+    return RTLFS_OK;
+}
+
+// Enqueue good trace + transposes on s_main (stream work only; prepare_good first).
+int launch_good(rtlfs_ctx *ctx) {
+    const GoodLaunch &g = ctx->gl;
+    CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
+    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
+                         g.max_ch_s, true, ctx->d_err.p, ctx->s_main));
+    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
+                         ctx->d_err.p, ctx->s_main));
     for (Design *D : ctx->designs)
         CU(launch_transpose(D->d_gcol.p, D->d_rows.p, D->n_net, D->T, ctx->s_main));
     return RTLFS_OK;
+}
+
+int enqueue_good(rtlfs_ctx *ctx) {
+    int rc = prepare_good(ctx);
+    return rc != RTLFS_OK ? rc : launch_good(ctx);
 }
 
 int build_faults(rtlfs_ctx *ctx) {
@@ -596,9 +633,14 @@ int rtlfs_create(rtlfs_ctx **out, int device) {
         CU(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device));
         CU(cudaStreamCreateWithFlags(&ctx->s_main, cudaStreamNonBlocking));
         CU(cudaStreamCreateWithFlags(&ctx->s_heavy, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&ctx->s_good, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ctx->ev_wg, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&ctx->ev_wl, cudaEventDisableTiming));
         for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
+        for (auto &e : ctx->ev_graph) CU(cudaEventCreate(&e));
         CU(ctx->d_counters.reserve(4));
         CU(ctx->d_heads.reserve(8));
+        CU(cudaMallocHost(&ctx->p_small, 16 * sizeof(unsigned long long)));
         return RTLFS_OK;
     };
     rc = init();
@@ -615,9 +657,16 @@ void rtlfs_destroy(rtlfs_ctx *ctx) {
     for (Design *D : ctx->designs) delete D;
     ctx->designs.clear();
     for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+    for (auto &e : ctx->ev_graph) if (e) cudaEventDestroy(e);
+    for (auto &e : ctx->ev_win) if (e) cudaEventDestroy(e);
+    if (ctx->ev_wg) cudaEventDestroy(ctx->ev_wg);
+    if (ctx->ev_wl) cudaEventDestroy(ctx->ev_wl);
+    if (ctx->s_good) { cudaStreamSynchronize(ctx->s_good); cudaStreamDestroy(ctx->s_good); }
     if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
     if (ctx->s_heavy) cudaStreamDestroy(ctx->s_heavy);
     if (ctx->p_cycle) { cudaFreeHost(ctx->p_cycle); cudaFreeHost(ctx->p_port); cudaFreeHost(ctx->p_det); cudaFreeHost(ctx->p_load); }
+    if (ctx->p_small) cudaFreeHost(ctx->p_small);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     delete ctx;
 }
 
@@ -689,7 +738,10 @@ static int run_good_only(rtlfs_ctx *ctx) {
         if (!D->has_stim) return fail(ctx, RTLFS_E_STATE, "a design has no stimulus");
     int rc = enqueue_good(ctx);
     if (rc != RTLFS_OK) return rc;
+    uint32_t err = 0;
+    CU(cudaMemcpyAsync(&err, ctx->d_err.p, sizeof(err), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
+    if (err) return fail(ctx, RTLFS_E_CUDA, "good-trace descriptor staging did not complete (bounded wait ran out)");
     for (Design *D : ctx->designs) D->trace_valid = true;
     return RTLFS_OK;
 }
@@ -733,10 +785,12 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         rc = ensure_sched_buffers(ctx);
         if (rc != RTLFS_OK) return rc;
     }
-    const uint32_t counters[4] = {n_heavy, 0u, 0u, 0u};
-    CU(cudaMemcpy(ctx->d_counters.p, counters, sizeof(counters), cudaMemcpyHostToDevice));
     rc = ensure_heavy_scratch(ctx, hblock, o.heavy_ctas);
     if (rc != RTLFS_OK) return rc;
+    rc = prepare_good(ctx);
+    if (rc != RTLFS_OK) return rc;
+    uint32_t *cinit = reinterpret_cast<uint32_t *>(ctx->p_small + 10);
+    cinit[0] = n_heavy; cinit[1] = 0; cinit[2] = 0; cinit[3] = 0;
     const auto t_host1 = std::chrono::steady_clock::now();
 
     DevFaults f = dev_faults(ctx);
@@ -758,68 +812,302 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     qi.counters = ctx->d_heads.p + 6;
     Queues qp = ql;
     qp.counters = ctx->d_heads.p + 6;
-
-    cudaEvent_t *ev = ctx->ev;
-    CU(cudaEventRecord(ev[0], ctx->s_main));
-    CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
-    if (F) CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
-    uint32_t launches = 0;
-    rc = enqueue_good(ctx);
-    if (rc != RTLFS_OK) return rc;
-    launches += 2 + (uint32_t)ctx->designs.size();
-    CU(cudaEventRecord(ev[1], ctx->s_main));
-    if (dev_sched) {
-        CU(launch_features(ctx->d_designs.p, f, ctx->d_static_ptrs.p, ctx->d_X.p, ctx->d_heur.p, ctx->s_main));
-        const float *score = ctx->d_heur.p;
-        if (use_mlp) {
-            CU(launch_mlp_forward(ctx->d_wb.p, ctx->d_X.p, F, ctx->d_pred.p, ctx->s_main));
-            score = ctx->d_pred.p;
-            ++launches;
-        }
-        CU(launch_order(score, F, ctx->d_mm.p, ctx->d_hist.p, ctx->d_order.p, n_heavy,
-                        ctx->d_init_items.p, ctx->s_main));
-        launches += 6 + (n_heavy ? 1 : 0);
-    }
-    CU(cudaEventRecord(ev[6], ctx->s_main));
     const int per_sm = light_max_blocks_per_sm(lcap, lblock);
     if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "light kernel cannot be resident");
     const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((ql.n_light + lblock - 1) / lblock,
                                                                    (int64_t)per_sm * ctx->n_sm));
     const int hgrid = (int)ctx->heavy_grid;
+    const int64_t lgrid_cap = (int64_t)per_sm * ctx->n_sm;
     HeavyScratch hs = heavy_view(ctx);
-    if (ql.n_light) { CU(launch_light(ctx->d_designs.p, f, ql, lcap, lblock, lgrid, ctx->s_main)); ++launches; }
-    CU(cudaEventRecord(ev[2], ctx->s_main));
-    CU(cudaStreamWaitEvent(ctx->s_heavy, ev[6], 0));
-    if (n_heavy) { CU(launch_heavy(ctx->d_designs.p, f, qi, hs, hblock, hgrid, ctx->s_heavy)); ++launches; }
-    CU(cudaStreamWaitEvent(ctx->s_heavy, ev[2], 0));
-    CU(cudaEventRecord(ev[3], ctx->s_heavy));
-    CU(launch_heavy(ctx->d_designs.p, f, qp, hs, hblock, hgrid, ctx->s_heavy));
-    ++launches;
-    CU(cudaEventRecord(ev[4], ctx->s_heavy));
-    CU(cudaStreamWaitEvent(ctx->s_main, ev[4], 0));
-    if (F) {
-        CU(cudaMemcpyAsync(ctx->p_cycle, ctx->d_cycle.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
-        CU(cudaMemcpyAsync(ctx->p_port, ctx->d_port.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
-        CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
-        CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
+    cudaEvent_t *ev = ctx->ev;
+    uint32_t launches = 0;
+
+    // Windowed campaign: every live fault advances through the same window of cycles.
+    uint32_t Tmax = 0, max_net = 0;
+    for (Design *D : ctx->designs) { Tmax = std::max(Tmax, D->T); max_net = std::max(max_net, D->n_net); }
+    const uint32_t W = o.window > 0 ? (uint32_t)o.window : 0;
+    const uint32_t nw = W ? (Tmax + W - 1) / W : 0;
+    if (W) {
+        const size_t Fn = std::max<size_t>(F, 1);
+        uint32_t mr = 1;
+        for (Design *D : ctx->designs) mr = std::max(mr, D->R);
+        CU(ctx->w_st_nreg.reserve(Fn));
+        CU(ctx->w_st_r.reserve(Fn * LIGHT_KR));
+        CU(ctx->w_st_v.reserve(Fn * LIGHT_KR));
+        CU(ctx->w_live0.reserve(Fn));
+        CU(ctx->w_live1.reserve(Fn));
+        CU(ctx->w_carry0.reserve(Fn));
+        CU(ctx->w_carry1.reserve(Fn));
+        const uint64_t pool_cap = std::min<uint64_t>((uint64_t)Fn * mr, (uint64_t)16 << 20);
+        CU(ctx->w_pool_r0.reserve(pool_cap));
+        CU(ctx->w_pool_r1.reserve(pool_cap));
+        CU(ctx->w_pool_v0.reserve(pool_cap));
+        CU(ctx->w_pool_v1.reserve(pool_cap));
+        ctx->w_pool_cap = pool_cap;
+        CU(ctx->w_cnt32.reserve(3 * (size_t)nw + 4));   // n_live, prom_end, n_carry | prom_total, n_light, zero
+        CU(ctx->w_cnt64.reserve(3 * (size_t)nw + 1));   // pool_top, light head, heavy head
+        while (ctx->ev_win.size() < 4 * (size_t)nw) {
+            cudaEvent_t e;
+            CU(cudaEventCreate(&e));
+            ctx->ev_win.push_back(e);
+        }
+        uint32_t *ci = reinterpret_cast<uint32_t *>(ctx->p_small + 10);
+        ci[0] = n_heavy;        // prom_total starts after the initial heavy items
+        ci[1] = F - n_heavy;    // faults in the first light window
+        ci[2] = 0;
+        ci[3] = 0;
     }
-    unsigned long long heads[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t cnts[4] = {0, 0, 0, 0};
-    CU(cudaMemcpyAsync(heads, ctx->d_heads.p, sizeof(heads), cudaMemcpyDeviceToHost, ctx->s_main));
-    CU(cudaMemcpyAsync(cnts, ctx->d_counters.p, sizeof(cnts), cudaMemcpyDeviceToHost, ctx->s_main));
-    CU(cudaEventRecord(ev[5], ctx->s_main));
+    const bool timed_windows = W && !o.use_graph;
+
+    // Windowed stream work (good trace on s_good, light on s_main, heavy on s_heavy).
+    auto enqueue_windowed = [&]() -> int {
+        launches = 0;
+        uint32_t *c32 = ctx->w_cnt32.p;
+        unsigned long long *c64 = ctx->w_cnt64.p;
+        uint32_t *prom_total = c32 + 3 * nw, *n_light0 = c32 + 3 * nw + 1, *zero = c32 + 3 * nw + 2;
+        CU(cudaEventRecord(ev[0], ctx->s_main));
+        CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
+        CU(cudaMemsetAsync(c32, 0, (3 * (size_t)nw + 4) * sizeof(uint32_t), ctx->s_main));
+        CU(cudaMemsetAsync(c64, 0, (3 * (size_t)nw + 1) * sizeof(unsigned long long), ctx->s_main));
+        CU(cudaMemcpyAsync(prom_total, ctx->p_small + 10, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
+        CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
+        if (F) {
+            CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
+            CU(cudaMemsetAsync(ctx->w_st_nreg.p, 0, F, ctx->s_main));
+        }
+        CU(cudaEventRecord(ctx->ev_wl, ctx->s_main));
+        CU(cudaStreamWaitEvent(ctx->s_good, ctx->ev_wl, 0));
+        CU(cudaStreamWaitEvent(ctx->s_heavy, ctx->ev_wl, 0));
+        const GoodLaunch &g = ctx->gl;
+        const uint32_t lblocks = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(((int64_t)F + lblock - 1) / lblock,
+                                                                                  (int64_t)lgrid_cap));
+        for (uint32_t w = 0; w < nw; ++w) {
+            const uint32_t t0 = w * W, t1 = std::min(t0 + W, Tmax);
+            // good trace of the window
+            CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
+                                 g.max_ch_s, true, ctx->d_err.p, ctx->s_good, t0, t1));
+            CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
+                                 ctx->d_err.p, ctx->s_good, t0, t1));
+            CU(launch_transpose_window(ctx->d_designs.p, (uint32_t)ctx->designs.size(), max_net, t0, t1, ctx->s_good));
+            launches += 3;
+            if (w == 0) CU(cudaEventRecord(ev[1], ctx->s_good));
+            CU(cudaEventRecord(ctx->ev_wg, ctx->s_good));
+            // light kernel of the window (after the scheduler for the first one)
+            CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_wg, 0));
+            if (w == 0) {
+                if (dev_sched) {
+                    CU(launch_features(ctx->d_designs.p, f, ctx->d_static_ptrs.p, ctx->d_X.p, ctx->d_heur.p,
+                                       ctx->s_main, t1));
+                    const float *score = ctx->d_heur.p;
+                    if (use_mlp) {
+                        CU(launch_mlp_forward(ctx->d_wb.p, ctx->d_X.p, F, ctx->d_pred.p, ctx->s_main));
+                        score = ctx->d_pred.p;
+                        ++launches;
+                    }
+                    CU(launch_order(score, F, ctx->d_mm.p, ctx->d_hist.p, ctx->d_order.p, n_heavy,
+                                    ctx->d_prom_items.p, ctx->s_main));
+                    launches += 6 + (n_heavy ? 1 : 0);
+                }
+                CU(cudaEventRecord(ev[6], ctx->s_main));
+            }
+            WinLight wl{};
+            wl.live_in = w == 0 ? ctx->d_order.p + n_heavy : (w & 1 ? ctx->w_live0.p : ctx->w_live1.p);
+            wl.n_live_in = w == 0 ? n_light0 : c32 + (w - 1);
+            wl.live_out = (w & 1) ? ctx->w_live1.p : ctx->w_live0.p;
+            wl.n_live_out = c32 + w;
+            wl.head = c64 + nw + w;
+            wl.prom = ctx->d_prom_items.p;
+            wl.prom_total = prom_total;
+            wl.prom_cap = F;
+            wl.st_nreg = ctx->w_st_nreg.p;
+            wl.st_r = ctx->w_st_r.p;
+            wl.st_v = ctx->w_st_v.p;
+            wl.F = F;
+            wl.t0 = t0;
+            wl.t1 = t1;
+            wl.budget_hit = ctx->d_heads.p + 3;
+            wl.fault_budget = o.fault_budget;
+            wl.counters = ctx->d_heads.p + 4;
+            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[0 * nw + w], ctx->s_main));
+            if (F) { CU(launch_light_window(ctx->d_designs.p, f, wl, lcap, lblock, (int)lblocks, ctx->s_main)); ++launches; }
+            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[1 * nw + w], ctx->s_main));
+            CU(cudaMemcpyAsync(c32 + nw + w, prom_total, sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->s_main));
+            CU(cudaEventRecord(ctx->ev_wl, ctx->s_main));
+            // heavy kernel of the window: carried heavy faults plus this window's promotions
+            CU(cudaStreamWaitEvent(ctx->s_heavy, ctx->ev_wl, 0));
+            WinHeavy wh{};
+            wh.carry_in = (w & 1) ? ctx->w_carry0.p : ctx->w_carry1.p;
+            wh.n_carry_in = w == 0 ? zero : c32 + 2 * nw + (w - 1);
+            wh.pool_r_in = (w & 1) ? ctx->w_pool_r0.p : ctx->w_pool_r1.p;
+            wh.pool_v_in = (w & 1) ? ctx->w_pool_v0.p : ctx->w_pool_v1.p;
+            wh.carry_out = (w & 1) ? ctx->w_carry1.p : ctx->w_carry0.p;
+            wh.n_carry_out = c32 + 2 * nw + w;
+            wh.pool_r_out = (w & 1) ? ctx->w_pool_r1.p : ctx->w_pool_r0.p;
+            wh.pool_v_out = (w & 1) ? ctx->w_pool_v1.p : ctx->w_pool_v0.p;
+            wh.pool_top_out = c64 + w;
+            wh.pool_cap = ctx->w_pool_cap;
+            wh.prom = ctx->d_prom_items.p;
+            wh.prom_begin = w == 0 ? zero : c32 + nw + (w - 1);
+            wh.prom_end = c32 + nw + w;
+            wh.head = c64 + 2 * nw + w;
+            wh.t0 = t0;
+            wh.t1 = t1;
+            wh.budget_hit = ctx->d_heads.p + 3;
+            wh.fault_budget = o.fault_budget;
+            wh.counters = ctx->d_heads.p + 6;
+            wh.err = ctx->d_err.p;
+            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[2 * nw + w], ctx->s_heavy));
+            CU(launch_heavy_window(ctx->d_designs.p, f, wh, hs, hblock, hgrid, ctx->s_heavy));
+            ++launches;
+            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[3 * nw + w], ctx->s_heavy));
+        }
+        CU(cudaEventRecord(ev[2], ctx->s_main));
+        CU(cudaEventRecord(ev[3], ctx->s_good));
+        CU(cudaStreamWaitEvent(ctx->s_main, ev[3], 0));
+        CU(cudaEventRecord(ev[4], ctx->s_heavy));
+        CU(cudaStreamWaitEvent(ctx->s_main, ev[4], 0));
+        if (F) {
+            CU(cudaMemcpyAsync(ctx->p_cycle, ctx->d_cycle.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+            CU(cudaMemcpyAsync(ctx->p_port, ctx->d_port.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+            CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
+            CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
+        }
+        CU(cudaMemcpyAsync(ctx->p_small, ctx->d_heads.p, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->s_main));
+        // counts reported as in the unwindowed form: [0] initial heavy, [1] promoted
+        CU(cudaMemcpyAsync(ctx->p_small + 8, prom_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_small + 12, ctx->d_err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaEventRecord(ev[5], ctx->s_main));
+        return RTLFS_OK;
+    };
+
+    // The campaign's stream work: no allocation, no synchronous copy, so that it can be
+    // captured into a CUDA graph and replayed.
+    auto enqueue = [&]() -> int {
+        launches = 0;
+        CU(cudaEventRecord(ev[0], ctx->s_main));
+        CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->d_counters.p, cinit, 4 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
+        if (F) CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
+        int r2 = launch_good(ctx);
+        if (r2 != RTLFS_OK) return r2;
+        launches += 2 + (uint32_t)ctx->designs.size();
+        CU(cudaEventRecord(ev[1], ctx->s_main));
+        if (dev_sched) {
+            CU(launch_features(ctx->d_designs.p, f, ctx->d_static_ptrs.p, ctx->d_X.p, ctx->d_heur.p, ctx->s_main));
+            const float *score = ctx->d_heur.p;
+            if (use_mlp) {
+                CU(launch_mlp_forward(ctx->d_wb.p, ctx->d_X.p, F, ctx->d_pred.p, ctx->s_main));
+                score = ctx->d_pred.p;
+                ++launches;
+            }
+            CU(launch_order(score, F, ctx->d_mm.p, ctx->d_hist.p, ctx->d_order.p, n_heavy,
+                            ctx->d_init_items.p, ctx->s_main));
+            launches += 6 + (n_heavy ? 1 : 0);
+        }
+        CU(cudaEventRecord(ev[6], ctx->s_main));
+        if (ql.n_light) { CU(launch_light(ctx->d_designs.p, f, ql, lcap, lblock, lgrid, ctx->s_main)); ++launches; }
+        CU(cudaEventRecord(ev[2], ctx->s_main));
+        CU(cudaStreamWaitEvent(ctx->s_heavy, ev[6], 0));
+        if (n_heavy) { CU(launch_heavy(ctx->d_designs.p, f, qi, hs, hblock, hgrid, ctx->s_heavy)); ++launches; }
+        CU(cudaStreamWaitEvent(ctx->s_heavy, ev[2], 0));
+        CU(cudaEventRecord(ev[3], ctx->s_heavy));
+        CU(launch_heavy(ctx->d_designs.p, f, qp, hs, hblock, hgrid, ctx->s_heavy));
+        ++launches;
+        CU(cudaEventRecord(ev[4], ctx->s_heavy));
+        CU(cudaStreamWaitEvent(ctx->s_main, ev[4], 0));
+        if (F) {
+            CU(cudaMemcpyAsync(ctx->p_cycle, ctx->d_cycle.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+            CU(cudaMemcpyAsync(ctx->p_port, ctx->d_port.p, (size_t)F * 4, cudaMemcpyDeviceToHost, ctx->s_main));
+            CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
+            CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
+        }
+        CU(cudaMemcpyAsync(ctx->p_small, ctx->d_heads.p, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_small + 8, ctx->d_counters.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaMemcpyAsync(ctx->p_small + 12, ctx->d_err.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->s_main));
+        CU(cudaEventRecord(ev[5], ctx->s_main));
+        return RTLFS_OK;
+    };
+
+    if (o.use_graph) {
+        // Everything the captured work depends on by address or size.
+        std::vector<uint64_t> key = {F, n_heavy, ql.n_light, (uint64_t)lcap, (uint64_t)lblock,
+                                     (uint64_t)lgrid, (uint64_t)hblock, (uint64_t)hgrid,
+                                     (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W};
+        const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p,
+                              ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
+                              ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,
+                              ctx->d_bit.p, ctx->d_val.p, ctx->d_fdesign.p, ctx->p_cycle, ctx->p_port,
+                              ctx->p_det, ctx->p_load, ctx->h_fval.p, ctx->h_regr.p, ctx->h_regv.p,
+                              ctx->d_X.p, ctx->d_heur.p, ctx->d_pred.p, ctx->d_mm.p, ctx->d_hist.p,
+                              ctx->d_wb.p, ctx->d_static_ptrs.p, ctx->w_st_nreg.p, ctx->w_st_r.p,
+                              ctx->w_st_v.p, ctx->w_live0.p, ctx->w_live1.p, ctx->w_cnt32.p, ctx->w_cnt64.p,
+                              ctx->w_carry0.p, ctx->w_carry1.p, ctx->w_pool_r0.p, ctx->w_pool_r1.p,
+                              ctx->w_pool_v0.p, ctx->w_pool_v1.p};
+        for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
+        const GoodLaunch &g = ctx->gl;
+        key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
+                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv});
+        for (Design *D : ctx->designs)
+            key.insert(key.end(), {(uint64_t)(uintptr_t)D->d_rows.p, (uint64_t)(uintptr_t)D->d_gcol.p,
+                                   D->n_net, D->T});
+        if (!ctx->graph_exec || key != ctx->graph_key) {
+            if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(ctx->s_main, cudaStreamCaptureModeRelaxed));
+            int r2 = W ? enqueue_windowed() : enqueue();
+            cudaError_t ec = cudaStreamEndCapture(ctx->s_main, &graph);
+            if (r2 != RTLFS_OK) { if (graph) cudaGraphDestroy(graph); return r2; }
+            CU(ec);
+            cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CU(ei);
+            ctx->graph_key = key;
+            ctx->graph_launches = launches;
+        }
+        launches = ctx->graph_launches;
+        // events recorded inside a graph give no elapsed times: bracket the launch instead
+        CU(cudaEventRecord(ctx->ev_graph[0], ctx->s_main));
+        CU(cudaGraphLaunch(ctx->graph_exec, ctx->s_main));
+        CU(cudaEventRecord(ctx->ev_graph[1], ctx->s_main));
+    } else {
+        rc = W ? enqueue_windowed() : enqueue();
+        if (rc != RTLFS_OK) return rc;
+    }
     CU(cudaStreamSynchronize(ctx->s_main));
+    {
+        const uint32_t kerr = *reinterpret_cast<const uint32_t *>(ctx->p_small + 12);
+        if (kerr & 2u)
+            return fail(ctx, RTLFS_E_NOMEM, "heavy register-diff pool overflowed; run with window = 0");
+        if (kerr)
+            return fail(ctx, RTLFS_E_CUDA, "good-trace descriptor staging did not complete (bounded wait ran out)");
+    }
+    const unsigned long long *heads = ctx->p_small;
+    const uint32_t *cnts = reinterpret_cast<const uint32_t *>(ctx->p_small + 8);
     for (Design *D : ctx->designs) D->trace_valid = true;
 
     // Scatter results and counters.
     rtlfs_stats &st = ctx->stats;
     st = rtlfs_stats{};
-    st.total_ms = ev_ms(ev[0], ev[5]);
-    st.good_ms = ev_ms(ev[0], ev[1]);
-    st.prep_ms = ev_ms(ev[1], ev[6]) + std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
-    st.faulty_ms = ev_ms(ev[6], ev[4]);
-    st.light_ms = ev_ms(ev[6], ev[2]);
-    st.heavy_ms = ev_ms(ev[3], ev[4]);
+    if (o.use_graph) {   // whole campaign only; per-phase times are not available
+        st.total_ms = ev_ms(ctx->ev_graph[0], ctx->ev_graph[1]);
+        st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
+    } else if (W) {   // overlapped phases: each kernel's own summed duration
+        st.total_ms = ev_ms(ev[0], ev[5]);
+        st.good_ms = ev_ms(ev[0], ev[3]);
+        st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
+        for (uint32_t w = 0; w < nw; ++w) {
+            st.light_ms += ev_ms(ctx->ev_win[w], ctx->ev_win[nw + w]);
+            st.heavy_ms += ev_ms(ctx->ev_win[2 * nw + w], ctx->ev_win[3 * nw + w]);
+        }
+        st.faulty_ms = ev_ms(ev[1], ev[4]);
+    } else {
+        st.total_ms = ev_ms(ev[0], ev[5]);
+        st.good_ms = ev_ms(ev[0], ev[1]);
+        st.prep_ms = ev_ms(ev[1], ev[6]) + std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
+        st.faulty_ms = ev_ms(ev[6], ev[4]);
+        st.light_ms = ev_ms(ev[6], ev[2]);
+        st.heavy_ms = ev_ms(ev[3], ev[4]);
+    }
     st.promoted = cnts[1];
     st.heavy_initial = cnts[0];
     st.n_launches = launches;
@@ -901,8 +1189,11 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out) {
         CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
         CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
     }
+    uint32_t gerr = 0;
+    CU(cudaMemcpyAsync(&gerr, ctx->d_err.p, sizeof(gerr), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaEventRecord(ev[5], ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
+    if (gerr) return fail(ctx, RTLFS_E_CUDA, "good-trace descriptor staging did not complete (bounded wait ran out)");
     for (Design *D : ctx->designs) D->trace_valid = true;
     rtlfs_stats &st = ctx->stats;
     st = rtlfs_stats{};

@@ -17,8 +17,10 @@ enum : uint32_t {
 
 constexpr uint32_t NO_PORT = 0xFFFFFFFFu;
 
-// Threads of the good-trace CTA = maximum nodes per good-trace chunk.
+// Threads of the good-trace CTA = maximum nodes per good-trace chunk, and the number of
+// chunk descriptor buffers the CTA keeps in flight (TMA staging).
 constexpr uint32_t GOOD_BLOCK = 512;
+constexpr int GOOD_NBUF = 3;
 
 // Node descriptor, 16 bytes: x/y/z = operand net ids (CONST: y:x = value), w = meta.
 // meta bits: [0,4) op, [8,15) width 1..64, [16,24) k = shift amount, slice offset or
@@ -106,6 +108,8 @@ constexpr uint32_t HEAVY_DLIST = 512;
 // Fan-out ranges a heavy CTA collects per level before marking consumers together; a
 // range beyond this many is marked by the thread that kept the net.
 constexpr uint32_t HEAVY_FRANGE = 256;
+// Fan-out lists up to this long are marked by the thread that kept the net.
+constexpr uint32_t HEAVY_INLINE_FANOUT = 16;
 
 // Per-slot scratch of the heavy kernel (one slot per resident CTA).
 struct HeavyScratch {
@@ -115,10 +119,72 @@ struct HeavyScratch {
     uint32_t max_net, max_reg, max_node, max_levels;
 };
 
+// ---- windowed campaign (cycles processed in windows [t0, t1) by every live fault) ------
+// A heavy fault that reaches the end of a window carries its register diffs to the next
+// window through a pool: pool_r/pool_v[off .. off+nreg).
+struct HeavyCarry {
+    uint32_t fault;
+    uint32_t nreg;
+    uint64_t off;
+};
+
+struct WinLight {
+    const uint32_t *live_in;      // fault ids alive at t0
+    const uint32_t *n_live_in;    // device count of live_in
+    uint32_t *live_out;           // survivors at t1 (appended, order unspecified)
+    uint32_t *n_live_out;
+    unsigned long long *head;     // queue position in live_in (zero at run start)
+    HeavyItem *prom;              // promotions: appended at *prom_total
+    uint32_t *prom_total;
+    uint32_t prom_cap;
+    uint8_t *st_nreg;             // [F] register diffs carried between windows
+    uint32_t *st_r;               // [LIGHT_KR][F]
+    uint64_t *st_v;               // [LIGHT_KR][F]
+    uint32_t F, t0, t1;
+    unsigned long long *budget_hit;
+    uint64_t fault_budget;
+    unsigned long long *counters; // [0] evaluations, [1] fault-cycles
+};
+
+struct WinHeavy {
+    const HeavyCarry *carry_in;   // heavy faults alive at t0
+    const uint32_t *n_carry_in;
+    const uint32_t *pool_r_in;
+    const uint64_t *pool_v_in;
+    HeavyCarry *carry_out;
+    uint32_t *n_carry_out;
+    uint32_t *pool_r_out;
+    uint64_t *pool_v_out;
+    unsigned long long *pool_top_out;
+    uint64_t pool_cap;
+    const HeavyItem *prom;        // this window's promotions: prom[*prom_begin .. *prom_end)
+    const uint32_t *prom_begin;
+    const uint32_t *prom_end;
+    unsigned long long *head;
+    uint32_t t0, t1;
+    unsigned long long *budget_hit;
+    uint64_t fault_budget;
+    unsigned long long *counters;
+    uint32_t *err;                // bit 1: pool overflow
+};
+
 // Launchers (rtlfs_kernels.cu). All enqueue on `stream` and return the launch status.
+size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks);
+// Good trace of cycles [t_begin, min(t_end, T)) of every listed design; t_begin > 0
+// resumes from the trace row of cycle t_begin-1.
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              uint32_t max_chunks, bool use_smem, cudaStream_t stream);
+                              uint32_t max_chunks, bool use_smem, uint32_t *err,
+                              cudaStream_t stream, uint32_t t_begin = 0,
+                              uint32_t t_end = 0xFFFFFFFFu);
+// rows -> gcol for cycles [t0, t1) of all n_designs designs (one launch).
+cudaError_t launch_transpose_window(const DevDesign *d_designs, uint32_t n_designs,
+                                    uint32_t max_net, uint32_t t0, uint32_t t1,
+                                    cudaStream_t stream);
+cudaError_t launch_light_window(const DevDesign *d_designs, DevFaults f, WinLight w, int cap,
+                                int block, int grid, cudaStream_t stream);
+cudaError_t launch_heavy_window(const DevDesign *d_designs, DevFaults f, WinHeavy w,
+                                HeavyScratch s, int block, int grid, cudaStream_t stream);
 cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,
                              cudaStream_t stream);
 cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int cap, int block,

@@ -63,47 +63,89 @@ __device__ __forceinline__ uint64_t force_bit(uint64_t x, uint64_t bm, bool sv) 
 // ===================================================================================
 // Good-machine trace. One CTA per design walks the cycles; inside a cycle the nodes of
 // one topological level are independent and are spread over the threads, with a
-// barrier between levels. The node list is cut into chunks of at most GOOD_BLOCK nodes that
-// never straddle a level, so every thread owns at most one node per chunk and the same
-// node in every cycle; each thread keeps the descriptors of its next three chunks in
-// registers (a prefetch ring that wraps into the next cycle), so descriptor loads are
-// off the critical path. Net values of the current cycle live in shared memory when
-// they fit (USE_SMEM) and are streamed to the row-major trace rows[t][net].
+// barrier between levels. The node list is cut into chunks of at most GOOD_BLOCK nodes
+// that never straddle a level, so every thread owns at most one node per chunk. The
+// chunks' descriptors are staged into shared memory by TMA bulk copies (cp.async.bulk,
+// completion counted on an mbarrier per buffer), GOOD_NBUF chunks ahead of use and
+// wrapping into the next cycle, so no thread ever waits on a global descriptor load.
+// Net values of the current cycle live in shared memory when they fit (USE_SMEM) and are
+// streamed to the row-major trace rows[t][net]. A staging wait that exceeds its bound
+// sets *err and lets the kernel run to its end (the host then reports a CUDA error).
 // ===================================================================================
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tma_issue(uint64_t *mbar, void *dst, const void *src, uint32_t bytes) {
+    const uint32_t mb = smem_u32(mbar);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(mb) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    const uint32_t mb = smem_u32(mbar);
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <bool USE_SMEM>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(GOOD_BLOCK, 1)
 good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
-                  uint32_t max_net, uint32_t max_reg, uint32_t max_chunks) {
-    extern __shared__ uint64_t gsm[];
+                  uint32_t max_net, uint32_t max_reg, uint32_t max_chunks, uint32_t *err,
+                  uint32_t t_begin, uint32_t t_end) {
+    extern __shared__ __align__(128) uint64_t gsm[];
     const DevDesign &D = designs[list[blockIdx.x]];
-    const uint32_t I = D.I, R = D.R, IR = I + R, n_net = D.n_net, T = D.T, NC = D.n_chunks;
+    const uint32_t I = D.I, R = D.R, IR = I + R, n_net = D.n_net, NC = D.n_chunks;
+    const uint32_t T = min(D.T, t_end);   // last cycle (exclusive) of this launch
+    if (t_begin >= T) return;
     const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const size_t vwords = USE_SMEM ? (size_t)max_net + max_reg : 0;   // u64 words of values
     uint64_t *val = gsm;                                     // [max_net] when USE_SMEM
     uint64_t *qn = gsm + (USE_SMEM ? max_net : 0);           // [max_reg] when USE_SMEM
-    uint2 *ch = reinterpret_cast<uint2 *>(gsm + (USE_SMEM ? (size_t)max_net + max_reg : 0));
+    uint4 *stage = reinterpret_cast<uint4 *>(gsm + ((vwords + 15) & ~(size_t)15));   // [NBUF][GOOD_BLOCK]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stage + GOOD_NBUF * GOOD_BLOCK);  // [NBUF]
+    uint2 *ch = reinterpret_cast<uint2 *>(mbar + GOOD_NBUF);                        // [max_chunks]
     for (uint32_t c = tid; c < NC; c += B) ch[c] = D.chunks[c];
+    if (tid == 0) {
+        for (int b = 0; b < GOOD_NBUF; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     // this thread's input and its first two registers, kept in registers for every cycle
     const uint64_t in_mask = tid < I ? wmask(D.net_w[tid]) : 0ull;
     const uint32_t r0 = tid, r1 = tid + B;
     const uint32_t rd0 = r0 < R ? D.reg_d[r0] : 0, rd1 = r1 < R ? D.reg_d[r1] : 0;
     const uint64_t rm0 = r0 < R ? wmask(D.net_w[I + r0]) : 0, rm1 = r1 < R ? wmask(D.net_w[I + r1]) : 0;
+    if (USE_SMEM && t_begin > 0) {   // resume: register values of t_begin from row t_begin-1
+        const uint64_t *prev = D.rows + (size_t)(t_begin - 1) * n_net;
+        for (uint32_t r = tid; r < R; r += B) qn[r] = prev[D.reg_d[r]] & wmask(D.net_w[I + r]);
+    }
     __syncthreads();
 
-    auto fetch = [&](uint32_t c) -> uint4 {
-        const uint2 b = ch[c];
-        const uint32_t n = b.x + tid;
-        return n < (b.y & 0x7FFFFFFFu) ? __ldg(D.desc + n) : make_uint4(0, 0, 0, 0xFFFFFFFFu);
+    const uint64_t total = (uint64_t)(T - t_begin) * NC;   // chunk instances of this launch
+    uint32_t cf = 0;                           // chunk index of the next issue (wraps)
+    auto issue = [&](uint64_t k) {             // thread 0: chunk instance k into its buffer
+        const uint2 b = ch[cf];
+        const uint32_t n = (b.y & 0x7FFFFFFFu) - b.x;
+        tma_issue(mbar + (k % GOOD_NBUF), stage + (k % GOOD_NBUF) * GOOD_BLOCK, D.desc + b.x, n * 16u);
+        cf = cf + 1 == NC ? 0 : cf + 1;
     };
-    uint4 d0 = make_uint4(0, 0, 0, 0xFFFFFFFFu), d1 = d0, d2 = d0;
-    uint32_t cf = 0;                 // next chunk to prefetch (wraps)
-    if (NC) {
-        d0 = fetch(cf); cf = cf + 1 == NC ? 0 : cf + 1;
-        d1 = fetch(cf); cf = cf + 1 == NC ? 0 : cf + 1;
-        d2 = fetch(cf); cf = cf + 1 == NC ? 0 : cf + 1;
-    }
-    uint64_t s_next = (tid < I) ? __ldg(D.stim + tid) : 0ull;
+    if (tid == 0)
+        for (uint64_t k = 0; k < GOOD_NBUF && k < total; ++k) issue(k);
+    uint64_t kc = 0;                           // chunk instance being consumed
+    uint64_t s_next = (tid < I) ? __ldg(D.stim + (size_t)t_begin * I + tid) : 0ull;
+    bool failed = false;
 
-    for (uint32_t t = 0; t < T; ++t) {
+    for (uint32_t t = t_begin; t < T; ++t) {
         uint64_t *row = D.rows + (size_t)t * n_net;
         const uint64_t s_cur = s_next;
         if (tid < I && t + 1 < T) s_next = __ldg(D.stim + (size_t)(t + 1) * I + tid);
@@ -117,10 +159,13 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
             row[i] = v;
         }
         __syncthreads();
-        for (uint32_t c = 0; c < NC; ++c) {
+        for (uint32_t c = 0; c < NC; ++c, ++kc) {
             const uint2 b = ch[c];
-            if (d0.w != 0xFFFFFFFFu) {
-                const uint32_t n = b.x + tid;
+            const uint32_t buf = (uint32_t)(kc % GOOD_NBUF);
+            const bool staged = mbar_wait(mbar + buf, (uint32_t)((kc / GOOD_NBUF) & 1));
+            const uint32_t n = b.x + tid;
+            if (staged && n < (b.y & 0x7FFFFFFFu)) {
+                const uint4 d0 = stage[buf * GOOD_BLOCK + tid];
                 const uint32_t op = meta_op(d0.w);
                 const int no = n_operands(op);
                 uint64_t a = 0, bb = 0, cc = 0;
@@ -131,18 +176,24 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
                 if (USE_SMEM) val[IR + n] = v;
                 row[IR + n] = v;
             }
-            if (b.y & 0x80000000u) __syncthreads();
-            d0 = d1;
-            d1 = d2;
-            d2 = fetch(cf);
-            cf = cf + 1 == NC ? 0 : cf + 1;
+            // every thread is done with this buffer (and every wait succeeded): refill it
+            if (!__syncthreads_and(staged)) { failed = true; break; }
+            if (tid == 0 && kc + GOOD_NBUF < total) issue(kc + GOOD_NBUF);
         }
+        if (failed) break;
         if (USE_SMEM) {
             if (r0 < R) qn[r0] = val[rd0] & rm0;
             if (r1 < R) qn[r1] = val[rd1] & rm1;
             for (uint32_t r = tid + 2 * B; r < R; r += B) qn[r] = val[D.reg_d[r]] & wmask(D.net_w[I + r]);
         }
         __syncthreads();
+    }
+    if (failed && tid == 0) {
+        // a staging wait ran out: report it, give the copies still in flight a bounded
+        // chance to land, and leave
+        atomicOr(err, 1u);
+        for (uint64_t k = kc; k < kc + GOOD_NBUF && k < total; ++k)
+            mbar_wait(mbar + (k % GOOD_NBUF), (uint32_t)((k / GOOD_NBUF) & 1));
     }
 }
 
@@ -160,6 +211,25 @@ __global__ void transpose_kernel(uint64_t *__restrict__ gcol, const uint64_t *__
     for (uint32_t j = ty; j < 32; j += blockDim.y) {
         const uint32_t n = n0 + j, t = t0 + tx;
         if (n < n_net && t < T) gcol[(size_t)n * T + t] = tile[tx][j];
+    }
+}
+
+// Window transpose: rows[t][net] -> gcol[net][t] for t in [t0, t1), every design (z).
+__global__ void transpose_window_kernel(const DevDesign *__restrict__ designs, uint32_t t0, uint32_t t1) {
+    __shared__ uint64_t tile[32][33];
+    const DevDesign &D = designs[blockIdx.z];
+    const uint32_t n_net = D.n_net, T = min(D.T, t1);
+    const uint32_t n0 = blockIdx.x * 32, tb = t0 + blockIdx.y * 32;
+    if (n0 >= n_net || tb >= T) return;
+    const uint32_t tx = threadIdx.x, ty = threadIdx.y;
+    for (uint32_t j = ty; j < 32; j += blockDim.y) {
+        const uint32_t t = tb + j, n = n0 + tx;
+        if (t < T && n < n_net) tile[j][tx] = D.rows[(size_t)t * n_net + n];
+    }
+    __syncthreads();
+    for (uint32_t j = ty; j < 32; j += blockDim.y) {
+        const uint32_t n = n0 + j, t = tb + tx;
+        if (n < n_net && t < T) D.gcol[(size_t)n * D.T + t] = tile[tx][j];
     }
 }
 
@@ -223,7 +293,7 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
             if (nreg == 0) {
                 // Skip quiescent cycles: nothing differs unless the site bit is activated.
                 // Four cycles per step, loads issued together.
-                const uint64_t want = sv ? 0ull : bm;   // good bit value that is not activated
+                const uint64_t want = sv ? bm : 0ull;   // site bit equal to the stuck value: quiescent
                 while (t + 4 <= T) {
                     const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
                     const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
@@ -406,9 +476,10 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
 // empty level costs one shared read), a bitmap over the nets (differs this cycle) and a
 // list of fan-out ranges to expand. Differing values live in per-slot global scratch.
 // Each level runs in two phases: (1) the dirty nodes of the level are evaluated in
-// parallel -- the fault's bad gates split over the threads -- and every kept net appends
-// its fan-out range; (2) all threads mark the consumers of those ranges together, so a
-// control net with thousands of readers costs a few passes instead of one thread's loop.
+// parallel -- the fault's bad gates split over the threads -- and a kept net marks its
+// consumers itself when it has few, or appends its fan-out range when it has many; (2)
+// all threads mark the consumers of the long ranges together, so a control net with
+// thousands of readers costs a few passes instead of one thread's loop.
 // ===================================================================================
 __global__ void __launch_bounds__(1024)
 heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
@@ -418,7 +489,9 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
     uint32_t *cnt = bm + nwn;            // [max_levels] dirty nodes per level
     uint32_t *dbm = cnt + S.max_levels;  // [nwd] nets that differ this cycle
     uint32_t *dlist = dbm + nwd;         // [HEAVY_DLIST] words of dbm to clear
-    uint2 *frange = reinterpret_cast<uint2 *>(dlist + HEAVY_DLIST);   // [HEAVY_FRANGE]
+    // the range ring holds 8-byte entries: start it on an even word (heavy_smem_bytes agrees)
+    const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + 1) & ~(size_t)1;
+    uint2 *frange = reinterpret_cast<uint2 *>(hsm + fr_words);   // [HEAVY_FRANGE]
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
     __shared__ unsigned long long s_load;
@@ -522,10 +595,12 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                 }
                 const uint32_t p = ni_port(ni.w);
                 if (p != NI_NO_PORT) atomicMin(&s_minport, p);
-                if (ni.y > ni.x) {
+                if (ni.y - ni.x > HEAVY_INLINE_FANOUT) {   // long list: all threads share it
                     const uint32_t k = atomicAdd(&s_nfr, 1u);
                     if (k - fr_begin < HEAVY_FRANGE) frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
                     else mark_range(ni.x, ni.y, 0, 1);   // ring full: mark here
+                } else if (ni.y > ni.x) {
+                    mark_range(ni.x, ni.y, 0, 1);
                 }
                 uint32_t nr = ni_nreg(ni.w);
                 if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
@@ -639,6 +714,515 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
             if (status == 3) atomicAdd(q.budget_hit, 1ull);
             atomicAdd(q.counters + 0, (unsigned long long)s_load);
             const uint32_t t_end = status == 1 ? t + 1 : min(t, T);
+            atomicAdd(q.counters + 1, (unsigned long long)(t_end - t_start));
+        }
+        __syncthreads();
+    }
+}
+
+// Windowed light kernel: the light kernel over cycles [t0, t1) of the live faults;
+// survivors carry their register diffs to the next window.
+template <int KR, int KD, int KH>
+__global__ void __launch_bounds__(256, 1)
+light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight q) {
+    extern __shared__ __align__(16) unsigned char lsm[];
+    const uint32_t B = blockDim.x, tx = threadIdx.x;
+    uint64_t *rv = reinterpret_cast<uint64_t *>(lsm);           // [2][KR][B]
+    uint64_t *dv = rv + 2 * KR * B;                              // [KD][B]
+    uint32_t *rr = reinterpret_cast<uint32_t *>(dv + KD * B);   // [2][KR][B]
+    uint32_t *dn = rr + 2 * KR * B;                              // [KD][B]
+    uint32_t *hp = dn + KD * B;                                  // [KH][B]
+#define RV(bf, k) rv[((bf) * KR + (k)) * B + tx]
+#define RR(bf, k) rr[((bf) * KR + (k)) * B + tx]
+#define DV(k) dv[(k) * B + tx]
+#define DN(k) dn[(k) * B + tx]
+#define HP(k) hp[(k) * B + tx]
+
+    const uint32_t n_live = *q.n_live_in;
+    const uint32_t lane = tx & 31u;
+    for (;;) {
+        const unsigned long long qi = atomicAdd(q.head, 1ull);
+        if (qi >= n_live) break;
+        const uint32_t fid = q.live_in[qi];
+        const DevDesign &D = designs[f.design[fid]];
+        const uint32_t I = D.I, IR = D.I + D.R, T = D.T;
+        const uint32_t tend = min(q.t1, T);     // this window ends at tend
+        const uint64_t *__restrict__ gcol = D.gcol;
+        const uint4 *__restrict__ netinfo = D.netinfo;
+        const uint4 *__restrict__ desc = D.desc;
+        const uint32_t *__restrict__ fo_idx = D.fo_idx;
+        const uint32_t site = f.site[fid];
+        const uint32_t bit = f.bit[fid];
+        const bool sv = f.val[fid] != 0;
+        const uint64_t bm = 1ull << bit;
+        const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
+        const uint32_t site_node = site >= IR ? site - IR : 0xFFFFFFFFu;
+
+        uint32_t t = q.t0, nreg = q.st_nreg[fid], cur = 0;
+        for (uint32_t k = 0; k < nreg; ++k) {   // register diffs carried from the last window
+            RR(0, k) = q.st_r[(size_t)k * q.F + fid];
+            RV(0, k) = q.st_v[(size_t)k * q.F + fid];
+        }
+        const uint64_t load_before = f.load[fid];
+        uint64_t load = 0;
+        int status = 0;                 // 1 detected, 2 promoted, 3 budget
+        int32_t det_cycle = -1, det_port = -1;
+
+        for (;;) {
+            if (nreg == 0) {
+                // Skip quiescent cycles: nothing differs unless the site bit is activated.
+                // Four cycles per step, loads issued together.
+                const uint64_t want = sv ? bm : 0ull;   // site bit equal to the stuck value: quiescent
+                while (t + 4 <= tend) {
+                    const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
+                    const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
+                    if ((g0 & bm) != want) break;
+                    if ((g1 & bm) != want) { t += 1; break; }
+                    if ((g2 & bm) != want) { t += 2; break; }
+                    if ((g3 & bm) != want) { t += 3; break; }
+                    t += 4;
+                }
+                if (t + 4 > tend) {
+                    while (t < tend && (__ldg(scol + t) & bm) == want) ++t;
+                }
+                if (t >= tend) break;
+            }
+            const uint32_t nb = cur ^ 1u;
+            uint32_t nd = 0, nh = 0, nreg_new = 0, minport = NI_NO_PORT;
+            uint64_t filter = 0;
+            bool ovf = false;
+            const uint64_t load_at_cycle_start = load;   // the heavy kernel redoes a promoted cycle
+
+            auto heap_push = [&](uint32_t x) {
+                if (nh >= (uint32_t)KH) { ovf = true; return; }
+                uint32_t i = nh++;
+                while (i > 0) {
+                    const uint32_t p = (i - 1) >> 1;
+                    const uint32_t hpv = HP(p);
+                    if (hpv <= x) break;
+                    HP(i) = hpv;
+                    i = p;
+                }
+                HP(i) = x;
+            };
+            auto heap_pop = [&]() -> uint32_t {
+                const uint32_t top = HP(0);
+                const uint32_t x = HP(--nh);
+                uint32_t i = 0;
+                for (;;) {
+                    uint32_t c = 2 * i + 1;
+                    if (c >= nh) break;
+                    uint32_t cv = HP(c);
+                    if (c + 1 < nh) {
+                        const uint32_t cv2 = HP(c + 1);
+                        if (cv2 < cv) { cv = cv2; ++c; }
+                    }
+                    if (x <= cv) break;
+                    HP(i) = cv;
+                    i = c;
+                }
+                if (nh > 0) HP(i) = x;
+                return top;
+            };
+            // Keep net (faulty v, good g, record ni): diff entry, detection, fan-out, latch.
+            auto add_diff = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
+                if (nd >= (uint32_t)KD) { ovf = true; return; }
+                DN(nd) = net;
+                DV(nd) = v;
+                ++nd;
+                filter |= 1ull << (net & 63u);
+                const uint32_t p = ni_port(ni.w);
+                minport = p < minport ? p : minport;
+                if (ni.y - ni.x > (uint32_t)KH) { ovf = true; return; }
+                for (uint32_t e = ni.x; e < ni.y; e += 4) {
+                    // four independent loads in flight, then the pushes
+                    const uint32_t c0 = __ldg(fo_idx + e);
+                    const uint32_t c1 = e + 1 < ni.y ? __ldg(fo_idx + e + 1) : 0xFFFFFFFFu;
+                    const uint32_t c2 = e + 2 < ni.y ? __ldg(fo_idx + e + 2) : 0xFFFFFFFFu;
+                    const uint32_t c3 = e + 3 < ni.y ? __ldg(fo_idx + e + 3) : 0xFFFFFFFFu;
+                    heap_push(c0);
+                    if (c1 != 0xFFFFFFFFu) heap_push(c1);
+                    if (c2 != 0xFFFFFFFFu) heap_push(c2);
+                    if (c3 != 0xFFFFFFFFu) heap_push(c3);
+                }
+                uint32_t nr = ni_nreg(ni.w);
+                if (nr) {
+                    if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                    for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
+                        const uint32_t r = __ldg(D.dreg_idx + e);
+                        const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                        const uint64_t qv = v & wm;
+                        if (qv != (g & wm)) {
+                            if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
+                            RR(nb, nreg_new) = r;
+                            RV(nb, nreg_new) = qv;
+                            ++nreg_new;
+                        }
+                    }
+                }
+            };
+            auto lookup = [&](uint32_t x) -> uint64_t {
+                if ((filter >> (x & 63u)) & 1ull) {
+                    for (uint32_t k = 0; k < nd; ++k)
+                        if (DN(k) == x) return DV(k);
+                }
+                return __ldg(gcol + (size_t)x * T + t);
+            };
+
+            bool site_seeded = false;
+            for (uint32_t k = 0; k < nreg && !ovf; ++k) {
+                const uint32_t net = I + RR(cur, k);
+                uint64_t qv = RV(cur, k);
+                if (net == site) { qv = force_bit(qv, bm, sv); site_seeded = true; }
+                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+                if (qv != g) add_diff(net, qv, g, __ldg(netinfo + net));
+            }
+            if (site < IR && !site_seeded && !ovf) {
+                const uint64_t g = __ldg(scol + t);
+                const uint64_t fv = force_bit(g, bm, sv);
+                if (fv != g) add_diff(site, fv, g, __ldg(netinfo + site));
+            }
+            if (site_node != 0xFFFFFFFFu && !ovf) heap_push(site_node);
+            uint32_t last = 0xFFFFFFFFu;
+            while (nh > 0 && !ovf) {
+                const uint32_t n = heap_pop();
+                if (n == last) continue;
+                last = n;
+                const uint32_t net = IR + n;
+                // independent loads first: descriptor, net record, good value
+                const uint4 d = __ldg(desc + n);
+                const uint4 ni = __ldg(netinfo + net);
+                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+                const uint32_t op = meta_op(d.w);
+                const int no = n_operands(op);
+                uint64_t a = 0, b = 0, c = 0;
+                if (no >= 1) a = lookup(d.x);
+                if (no >= 2) b = lookup(d.y);
+                if (no >= 3) c = lookup(d.z);
+                uint64_t v = eval_op(d, a, b, c);
+                if (n == site_node) v = force_bit(v, bm, sv);
+                ++load;
+                if (v != g) add_diff(net, v, g, ni);
+            }
+            if (ovf) {
+                const uint32_t p = atomicAdd(q.prom_total, 1u);
+                if (p < q.prom_cap) {
+                    HeavyItem &h = q.prom[p];
+                    h.fault = fid;
+                    h.t = t;
+                    h.nreg = nreg;
+                    for (uint32_t k = 0; k < nreg; ++k) {
+                        h.reg_r[k] = RR(cur, k);
+                        h.reg_v[k] = RV(cur, k);
+                    }
+                }
+                load = load_at_cycle_start;
+                status = 2;
+                break;
+            }
+            if (minport != NI_NO_PORT) {
+                det_cycle = (int32_t)t;
+                det_port = (int32_t)minport;
+                status = 1;
+                break;
+            }
+            cur = nb;
+            nreg = nreg_new;
+            if (++t >= tend) break;
+            if (q.fault_budget && load_before + load > q.fault_budget) { status = 3; break; }
+        }
+        f.load[fid] = load_before + load;
+        if (status == 1 || status == 3 || (status == 0 && tend == T)) {
+            f.res_det[fid] = status == 1 ? 1 : status == 3 ? 255 : 0;
+            f.res_cycle[fid] = det_cycle;
+            f.res_port[fid] = det_port;
+            if (status == 3) atomicAdd(q.budget_hit, 1ull);
+        } else if (status == 0) {
+            // alive at the end of the window: carry the register diffs, append to the
+            // survivors (warp-aggregated: one atomic per group of lanes arriving together)
+            q.st_nreg[fid] = (uint8_t)nreg;
+            for (uint32_t k = 0; k < nreg; ++k) {
+                q.st_r[(size_t)k * q.F + fid] = RR(cur, k);
+                q.st_v[(size_t)k * q.F + fid] = RV(cur, k);
+            }
+            const unsigned m = __activemask();
+            const int leader = __ffs(m) - 1;
+            const unsigned rank = __popc(m & ((1u << lane) - 1u));
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(q.n_live_out, (uint32_t)__popc(m));
+            base = __shfl_sync(m, base, leader);
+            q.live_out[base + rank] = fid;
+        }
+        // t is the first cycle not completed (a detection cycle counts as simulated)
+        atomicAdd(q.counters + 0, (unsigned long long)load);
+        atomicAdd(q.counters + 1, (unsigned long long)((status == 1 ? t + 1 : t) - q.t0));
+    }
+#undef RV
+#undef RR
+#undef DV
+#undef DN
+#undef HP
+}
+
+// Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
+// from the last window and those promoted in this one; survivors carry their register
+// diffs to the next window through the pool.
+__global__ void __launch_bounds__(1024)
+heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
+    uint32_t *bm = hsm;                  // [nwn] dirty nodes
+    uint32_t *cnt = bm + nwn;            // [max_levels] dirty nodes per level
+    uint32_t *dbm = cnt + S.max_levels;  // [nwd] nets that differ this cycle
+    uint32_t *dlist = dbm + nwd;         // [HEAVY_DLIST] words of dbm to clear
+    // the range ring holds 8-byte entries: start it on an even word (heavy_smem_bytes agrees)
+    const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + 1) & ~(size_t)1;
+    uint2 *frange = reinterpret_cast<uint2 *>(hsm + fr_words);   // [HEAVY_FRANGE]
+    __shared__ unsigned long long s_item, s_off;
+    __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
+    __shared__ unsigned long long s_load;
+    const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
+    uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
+    uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
+
+    for (uint32_t i = tid; i < nwn; i += B) bm[i] = 0;
+    for (uint32_t i = tid; i < S.max_levels; i += B) cnt[i] = 0;
+    for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
+    if (tid == 0) s_nfr = 0;
+    __syncthreads();
+
+    const uint32_t n_carry = *q.n_carry_in, pb = *q.prom_begin, pe = *q.prom_end;
+    const unsigned long long n_items = (unsigned long long)n_carry + (pe - pb);
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(q.head, 1ull);
+        __syncthreads();
+        const unsigned long long idx = s_item;
+        if (idx >= n_items) break;
+        const bool carried = idx < n_carry;
+        const HeavyCarry cin = carried ? q.carry_in[idx] : HeavyCarry{0, 0, 0};
+        const HeavyItem &it = q.prom[pb + (carried ? 0 : idx - n_carry)];
+        const uint32_t fid = carried ? cin.fault : it.fault;
+        const DevDesign &D = designs[f.design[fid]];
+        const uint32_t I = D.I, IR = D.I + D.R, T = D.T, NL = D.n_levels;
+        const uint32_t tend = min(q.t1, T);     // this window ends at tend
+        const uint64_t *__restrict__ gcol = D.gcol;
+        const uint4 *__restrict__ netinfo = D.netinfo;
+        const uint32_t *__restrict__ fo_idx = D.fo_idx;
+        const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
+        const uint32_t site = f.site[fid];
+        const uint32_t bit = f.bit[fid];
+        const bool sv = f.val[fid] != 0;
+        const uint64_t bmask = 1ull << bit;
+        const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
+        uint32_t t = carried ? q.t0 : it.t, nreg = carried ? cin.nreg : it.nreg, cur = 0;
+        const uint32_t t_start = t;
+        for (uint32_t k = tid; k < nreg; k += B) {
+            regR[k] = carried ? q.pool_r_in[cin.off + k] : it.reg_r[k];
+            regV[k] = carried ? q.pool_v_in[cin.off + k] : it.reg_v[k];
+        }
+        if (tid == 0) s_load = 0;
+        int status = 0;
+        int32_t det_cycle = -1, det_port = -1;
+        __syncthreads();
+
+        // Mark the consumers of one fan-out range (all threads of the CTA share the work
+        // when called from expand(); a single thread when the range list is full).
+        auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
+            for (uint32_t e = e0 + first; e < e1; e += step) {
+                const uint32_t c = __ldg(fo_idx + e);
+                const uint32_t lv = __ldg(fo_lvl + e);
+                const uint32_t b1 = 1u << (c & 31u);
+                const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
+                if (!(o2 & b1)) atomicAdd(&cnt[lv], 1u);
+            }
+        };
+        // Ranges live in a ring indexed by a per-cycle append counter s_nfr; fr_begin (the
+        // same in every thread, advanced only after a barrier) is the first unexpanded one.
+        uint32_t fr_begin = 0;
+        // Phase 2: every thread takes a share of every recorded range. Call after a barrier.
+        auto expand = [&]() {
+            const uint32_t end = s_nfr;
+            const uint32_t n = min(end - fr_begin, HEAVY_FRANGE);
+            for (uint32_t r = 0; r < n; ++r) {
+                const uint2 fr = frange[(fr_begin + r) % HEAVY_FRANGE];
+                mark_range(fr.x, fr.y, tid, B);
+            }
+            fr_begin = end;
+        };
+
+        for (;;) {
+            if (nreg == 0) {
+                if (warp == 0) {
+                    uint32_t found = tend;
+                    for (uint32_t tt = t; tt < tend; tt += 32) {
+                        const uint32_t u = tt + lane;
+                        bool act = false;
+                        if (u < tend) act = ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)sv;
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, act);
+                        if (bal) { found = tt + __ffs(bal) - 1; break; }
+                    }
+                    if (lane == 0) s_t = found;
+                }
+                __syncthreads();
+                t = s_t;
+                if (t >= tend) break;
+            }
+            const uint32_t nb = cur ^ 1u;
+            if (tid == 0) { s_nreg_new = 0; s_minport = NI_NO_PORT; s_site_seeded = 0; s_nd = 0; s_nfr = 0; }
+            fr_begin = 0;
+            __syncthreads();
+
+            // Keep a differing net: value, detection, latch, and its fan-out range.
+            auto keep = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
+                fval[net] = v;
+                const uint32_t wbit = 1u << (net & 31u);
+                const uint32_t old = atomicOr(&dbm[net >> 5], wbit);
+                if (!old) {   // first bit of this word: remember the word for clearing
+                    const uint32_t k = atomicAdd(&s_nd, 1u);
+                    if (k < HEAVY_DLIST) dlist[k] = net >> 5;
+                }
+                const uint32_t p = ni_port(ni.w);
+                if (p != NI_NO_PORT) atomicMin(&s_minport, p);
+                if (ni.y - ni.x > HEAVY_INLINE_FANOUT) {   // long list: all threads share it
+                    const uint32_t k = atomicAdd(&s_nfr, 1u);
+                    if (k - fr_begin < HEAVY_FRANGE) frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
+                    else mark_range(ni.x, ni.y, 0, 1);   // ring full: mark here
+                } else if (ni.y > ni.x) {
+                    mark_range(ni.x, ni.y, 0, 1);
+                }
+                uint32_t nr = ni_nreg(ni.w);
+                if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
+                    const uint32_t r = __ldg(D.dreg_idx + e);
+                    const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                    const uint64_t qv = v & wm;
+                    if (qv != (g & wm)) {
+                        const uint32_t k = atomicAdd(&s_nreg_new, 1u);
+                        regR[nb * S.max_reg + k] = r;
+                        regV[nb * S.max_reg + k] = qv;
+                    }
+                }
+            };
+            auto lookup = [&](uint32_t x) -> uint64_t {
+                if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
+                return __ldg(gcol + (size_t)x * T + t);
+            };
+
+            for (uint32_t k = tid; k < nreg; k += B) {
+                const uint32_t net = I + regR[cur * S.max_reg + k];
+                uint64_t qv = regV[cur * S.max_reg + k];
+                const uint4 ni = __ldg(netinfo + net);
+                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+                if (net == site) { qv = force_bit(qv, bmask, sv); s_site_seeded = 1; }
+                if (qv != g) keep(net, qv, g, ni);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                if (site < IR && !s_site_seeded) {
+                    const uint64_t g = __ldg(scol + t);
+                    const uint64_t fv = force_bit(g, bmask, sv);
+                    if (fv != g) keep(site, fv, g, __ldg(netinfo + site));
+                }
+                if (site >= IR) {
+                    const uint32_t c = site - IR;
+                    const uint32_t b1 = 1u << (c & 31u);
+                    const uint32_t old = atomicOr(&bm[c >> 5], b1);
+                    if (!(old & b1)) atomicAdd(&cnt[__ldg(D.node_level + c)], 1u);
+                }
+            }
+            __syncthreads();
+            expand();
+            __syncthreads();
+            uint32_t my_load = 0;
+            for (uint32_t L = 0; L < NL; ++L) {
+                if (cnt[L] == 0) continue;
+                const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
+                const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
+                for (uint32_t w = w0 + tid; w <= w1; w += B) {
+                    uint32_t m = 0xFFFFFFFFu;
+                    if (w == w0) m &= 0xFFFFFFFFu << (lo & 31u);
+                    if (w == w1 && (hi & 31u)) m &= (1u << (hi & 31u)) - 1u;
+                    if (!(bm[w] & m)) continue;
+                    uint32_t bits = atomicAnd(&bm[w], ~m) & m;
+                    while (bits) {
+                        const uint32_t j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const uint32_t n = (w << 5) + j;
+                        const uint32_t net = IR + n;
+                        // independent loads first: descriptor, net record, good value
+                        const uint4 d = __ldg(D.desc + n);
+                        const uint4 ni = __ldg(netinfo + net);
+                        const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+                        const uint32_t op = meta_op(d.w);
+                        const int no = n_operands(op);
+                        uint64_t a = 0, b = 0, c = 0;
+                        if (no >= 1) a = lookup(d.x);
+                        if (no >= 2) b = lookup(d.y);
+                        if (no >= 3) c = lookup(d.z);
+                        uint64_t v = eval_op(d, a, b, c);
+                        if (net == site) v = force_bit(v, bmask, sv);
+                        ++my_load;
+                        if (v != g) keep(net, v, g, ni);
+                    }
+                }
+                __syncthreads();
+                if (s_nfr != fr_begin) {   // uniform: read after the barrier
+                    expand();
+                    __syncthreads();
+                }
+                if (tid == 0) cnt[L] = 0;
+            }
+            if (my_load) atomicAdd(&s_load, (unsigned long long)my_load);
+            __syncthreads();
+            // clear the net bitmap for the next cycle
+            const uint32_t nd = s_nd;
+            if (nd <= HEAVY_DLIST) {
+                for (uint32_t k = tid; k < nd; k += B) dbm[dlist[k]] = 0;
+            } else {
+                for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
+            }
+            if (s_minport != NI_NO_PORT) {
+                det_cycle = (int32_t)t;
+                det_port = (int32_t)s_minport;
+                status = 1;
+                break;
+            }
+            nreg = s_nreg_new;
+            cur = nb;
+            if (++t >= tend) break;
+            if (q.fault_budget && (f.load[fid] + s_load) > q.fault_budget) { status = 3; break; }
+            __syncthreads();
+        }
+        __syncthreads();
+        const bool carry = status == 0 && tend < T;   // alive at the end of the window
+        if (carry) {
+            if (tid == 0) {
+                const unsigned long long off = atomicAdd(q.pool_top_out, (unsigned long long)nreg);
+                s_off = off + nreg <= q.pool_cap ? off : ~0ull;
+                if (s_off == ~0ull) atomicOr(q.err, 2u);
+            }
+            __syncthreads();
+            const unsigned long long off = s_off;
+            if (off != ~0ull) {
+                for (uint32_t k = tid; k < nreg; k += B) {
+                    q.pool_r_out[off + k] = regR[cur * S.max_reg + k];
+                    q.pool_v_out[off + k] = regV[cur * S.max_reg + k];
+                }
+                if (tid == 0) q.carry_out[atomicAdd(q.n_carry_out, 1u)] = HeavyCarry{fid, nreg, off};
+            }
+        }
+        if (tid == 0) {
+            f.load[fid] += s_load;
+            if (!carry) {
+                f.res_det[fid] = status == 1 ? 1 : status == 3 ? 255 : 0;
+                f.res_cycle[fid] = det_cycle;
+                f.res_port[fid] = det_port;
+            }
+            if (status == 3) atomicAdd(q.budget_hit, 1ull);
+            atomicAdd(q.counters + 0, (unsigned long long)s_load);
+            const uint32_t t_end = status == 1 ? t + 1 : min(t, tend);
             atomicAdd(q.counters + 1, (unsigned long long)(t_end - t_start));
         }
         __syncthreads();
@@ -773,25 +1357,32 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
 
 // ---- launchers -----------------------------------------------------------------------
 
+size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks) {
+    const size_t vwords = use_smem ? (size_t)max_net + max_reg : 0;
+    return (((vwords + 15) & ~(size_t)15) * sizeof(uint64_t)) + (size_t)GOOD_NBUF * GOOD_BLOCK * 16 +
+           GOOD_NBUF * sizeof(uint64_t) + (size_t)max_chunks * sizeof(uint2);
+}
+
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              uint32_t max_chunks, bool use_smem, cudaStream_t stream) {
+                              uint32_t max_chunks, bool use_smem, uint32_t *err, cudaStream_t stream,
+                              uint32_t t_begin, uint32_t t_end) {
     if (n_list == 0) return cudaSuccess;
-    const size_t smem = (use_smem ? ((size_t)max_net + max_reg) * sizeof(uint64_t) : 0) +
-                        (size_t)max_chunks * sizeof(uint2);
+    const size_t smem = good_smem_bytes(use_smem, max_net, max_reg, max_chunks);
     cudaError_t e;
     if (use_smem) {
         e = cudaFuncSetAttribute(good_trace_kernel<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         good_trace_kernel<true><<<n_list, GOOD_BLOCK, smem, stream>>>(d_designs, design_list, max_net,
-                                                               max_reg, max_chunks);
+                                                                     max_reg, max_chunks, err,
+                                                                     t_begin, t_end);
     } else {
         e = cudaFuncSetAttribute(good_trace_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         good_trace_kernel<false><<<n_list, GOOD_BLOCK, smem, stream>>>(d_designs, design_list, 0, 0,
-                                                                max_chunks);
+                                                                      max_chunks, err, t_begin, t_end);
     }
     return cudaGetLastError();
 }
@@ -800,6 +1391,14 @@ cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_ne
                              cudaStream_t stream) {
     dim3 grid((n_net + 31) / 32, (T + 31) / 32), block(32, 8);
     transpose_kernel<<<grid, block, 0, stream>>>(gcol, rows, n_net, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_window(const DevDesign *d_designs, uint32_t n_designs, uint32_t max_net,
+                                    uint32_t t0, uint32_t t1, cudaStream_t stream) {
+    if (!n_designs || t1 <= t0) return cudaSuccess;
+    dim3 grid((max_net + 31) / 32, (t1 - t0 + 31) / 32, n_designs), block(32, 8);
+    transpose_window_kernel<<<grid, block, 0, stream>>>(d_designs, t0, t1);
     return cudaGetLastError();
 }
 
@@ -840,6 +1439,22 @@ cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int 
     return cudaLaunchKernel(light_kernel_ptr(cap), dim3(grid), dim3(block), args, smem, stream);
 }
 
+template <int C>
+static void *light_window_fn() {
+    return (void *)light_window_kernel<LIGHT_CAPS[C][0], LIGHT_CAPS[C][1], LIGHT_CAPS[C][2]>;
+}
+
+cudaError_t launch_light_window(const DevDesign *d_designs, DevFaults f, WinLight w, int cap,
+                                int block, int grid, cudaStream_t stream) {
+    if (cap < 0 || cap > 2) return cudaErrorInvalidValue;
+    void *fn = cap == 0 ? light_window_fn<0>() : cap == 1 ? light_window_fn<1>() : light_window_fn<2>();
+    const size_t smem = light_smem(cap, block);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&d_designs, (void *)&f, (void *)&w};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
+}
+
 size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net) {
     size_t words = (size_t)(max_node + 31) / 32 + max_levels + (max_net + 31) / 32 + HEAVY_DLIST;
     words = (words + 1) & ~(size_t)1;   // 8-byte alignment of the range list
@@ -860,6 +1475,16 @@ cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, Heav
                                          (int)smem);
     if (e != cudaSuccess) return e;
     heavy_kernel<<<grid, block, smem, stream>>>(d_designs, f, q, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heavy_window(const DevDesign *d_designs, DevFaults f, WinHeavy w, HeavyScratch s,
+                                int block, int grid, cudaStream_t stream) {
+    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net);
+    cudaError_t e = cudaFuncSetAttribute(heavy_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    heavy_window_kernel<<<grid, block, smem, stream>>>(d_designs, f, w, s);
     return cudaGetLastError();
 }
 

@@ -20,15 +20,16 @@ namespace rtlfs {
 // toggle rate of the site bit from the good trace (lanes read 32 consecutive cycles).
 __global__ void features_kernel(const DevDesign *__restrict__ designs, DevFaults f,
                                 const float *__restrict__ const *net_static, float *X,
-                                float *heur) {
+                                float *heur, uint32_t t_limit) {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t lane = threadIdx.x & 31u;
     if (warp >= f.F) return;
     const uint32_t fid = warp;
     const uint32_t di = f.design[fid];
     const DevDesign &D = designs[di];
-    const uint32_t site = f.site[fid], bit = f.bit[fid], T = D.T;
-    const uint64_t *col = D.gcol + (size_t)site * T;
+    const uint32_t site = f.site[fid], bit = f.bit[fid];
+    const uint64_t *col = D.gcol + (size_t)site * D.T;
+    const uint32_t T = min(D.T, t_limit);   // cycles the toggle rate is measured over
     uint32_t toggles = 0;
     uint32_t prev_last = 0;   // bit at the last cycle of the previous 32-cycle block
     for (uint32_t t0 = 0; t0 < T; t0 += 32) {
@@ -303,10 +304,11 @@ __global__ void heavy_items_kernel(const uint32_t *order, uint32_t n_heavy, Heav
 // ---- launchers ------------------------------------------------------------------------
 
 cudaError_t launch_features(const DevDesign *d_designs, DevFaults f, const float *const *net_static,
-                            float *X, float *heur, cudaStream_t s) {
+                            float *X, float *heur, cudaStream_t s, uint32_t t_limit) {
     if (!f.F) return cudaSuccess;
     const uint32_t threads = 256, warps_per = threads / 32;
-    features_kernel<<<(f.F + warps_per - 1) / warps_per, threads, 0, s>>>(d_designs, f, net_static, X, heur);
+    features_kernel<<<(f.F + warps_per - 1) / warps_per, threads, 0, s>>>(d_designs, f, net_static, X, heur,
+                                                                          t_limit);
     return cudaGetLastError();
 }
 

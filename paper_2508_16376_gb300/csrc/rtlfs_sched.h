@@ -15,8 +15,9 @@ constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;          // 4608
 constexpr int MLP_PARAMS = MLP_OFF_B3 + 1;              // 4609
 constexpr uint32_t SORT_BUCKETS = 4096;
 
+// Toggle rates are measured over the first min(T, t_limit) cycles of each design.
 cudaError_t launch_features(const DevDesign *d_designs, DevFaults f, const float *const *net_static,
-                            float *X, float *heur, cudaStream_t s);
+                            float *X, float *heur, cudaStream_t s, uint32_t t_limit = 0xFFFFFFFFu);
 cudaError_t launch_mlp_forward(const void *wb, const float *X, uint32_t n, float *y, cudaStream_t s);
 size_t mlp_grad_smem();
 cudaError_t launch_mlp_grad(const void *wb, const float *X, const float *t, uint32_t n, float *grad,

@@ -291,3 +291,73 @@ def test_fault_budget_timeout_then_recovery():
         assert np.array_equal(det[ok], exp[0][ok]) and np.array_equal(res[0]["cycle"][ok], exp[1][ok])
         res2, _ = sim.run()
         assert_same(split(res2[0]), exp, "after budget")
+
+
+def test_cuda_graph_capture_and_replay():
+    """use_graph: the first run captures the launch sequence, later runs replay it; a new
+    fault list (new buffers) forces a new capture. Every result equals the oracle's."""
+    d = small_fsm_design(25)
+    stim = synth.stimulus(d, 300, 25, 0.1)
+    u1 = synth.sample_faults(d, 2000, 25)
+    u2 = synth.sample_faults(d, 2500, 26)
+    e1 = oracle.fault_sim(d, stim, u1, threads=16)
+    e2 = oracle.fault_sim(d, stim, u2, threads=16)
+    with Simulator(0) as sim:
+        sim.add(d, stim, u1)
+        for _ in range(3):
+            res, _ = sim.run(use_graph=1, heavy_frac=0.05)
+            assert_same(split(res[0]), e1, "graph replay")
+        sim.set_faults(0, u2)
+        for _ in range(2):
+            res, _ = sim.run(use_graph=1, heavy_frac=0.05)
+            assert_same(split(res[0]), e2, "graph after new faults")
+        res, _ = sim.run(use_graph=0)
+        assert_same(split(res[0]), e2, "no graph")
+
+
+# ---- windowed campaign ------------------------------------------------------------------
+
+@pytest.mark.parametrize("window", [1, 7, 64, 300])
+def test_windowed_matches_oracle(window):
+    """Every live fault advances through the same window of cycles; light survivors carry
+    their register diffs, heavy survivors go through the pool, promotions start in the
+    window they happen in. Window sizes from 1 cycle to the whole stimulus, ragged ends."""
+    d = small_fsm_design(27)
+    stim = synth.stimulus(d, 257, 27, 0.1)
+    u = synth.sample_faults(d, 3000, 27)
+    exp = oracle.fault_sim(d, stim, u, threads=16)
+    for kw in (dict(), dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN, light_cap=1)):
+        got = gpu_run(d, stim, u, want_load=True, window=window, **kw)
+        assert_same(got, exp, f"window {window} {kw}")
+    ref = gpu_run(d, stim, u, want_load=True)
+    assert np.array_equal(got[3], ref[3])      # same evaluations, windowed or not
+
+
+def test_windowed_batch_and_graph():
+    cases = []
+    for i, (n, T, F) in enumerate([(900, 130, 800), (2200, 61, 1200), (300, 200, 0), (1500, 1, 400)]):
+        d = small_fsm_design(60 + i, n, max(48, n // 10))
+        stim = synth.stimulus(d, T, 60 + i, 0.1)
+        f = synth.sample_faults(d, F, 60 + i) if F else synth.Faults(
+            np.zeros(0, np.uint32), np.zeros(0, np.uint8), np.zeros(0, np.uint8))
+        cases.append((d, stim, f))
+    with Simulator(0) as sim:
+        for d, stim, f in cases:
+            sim.add(d, stim, f)
+        runs = [sim.run(window=32, heavy_frac=0.05)[0], sim.run(window=32, use_graph=1)[0],
+                sim.run(window=32, use_graph=1)[0], sim.run(window=50, use_graph=1, light_cap=1)[0]]
+    for k, (d, stim, f) in enumerate(cases):
+        exp = oracle.fault_sim(d, stim, f, threads=8)
+        for res in runs:
+            assert_same(split(res[k]), exp, f"windowed batch {k}")
+
+
+def test_windowed_counter_golden():
+    rows = pins._load_counter_golden()
+    rows = rows[rows[:, 0] == 20]
+    f = synth.Faults(rows[:, 1].astype(np.uint32), rows[:, 2].astype(np.uint8), rows[:, 3].astype(np.uint8))
+    stim = np.zeros((20, 1), np.uint64)
+    for w in (1, 3, 8):
+        det, cyc, port = gpu_run(synth.counter4(), stim, f, window=w, heavy_frac=0.5)[:3]
+        assert np.array_equal(det, rows[:, 4]) and np.array_equal(cyc, rows[:, 5])
+        assert np.array_equal(port, rows[:, 6])
