@@ -256,6 +256,36 @@ int rtlfs_mlp_grad(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, f
 int rtlfs_mlp_train(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, uint32_t epochs,
                     uint32_t batch, float lr, float *final_loss);
 
+/* ---- allocation-free fault simulation -------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that must not allocate
+ * device memory where they run: work issued while a stream is captured into a CUDA graph
+ * (cudaMalloc would break the capture), latency-critical paths that cannot take an
+ * allocation or the synchronisation it may imply, and hosts whose device memory is owned
+ * by another allocator. It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * It simulates faults[n_faults] (device memory, the caller's net numbering) of design
+ * design_id against that design's good trace, one thread per fault (the plain GPU form),
+ * and writes results[n_faults] (device memory) with the same contract as rtlfs_run. The
+ * context must already hold the design's current good trace (from rtlfs_run or
+ * rtlfs_good_outputs after the last rtlfs_set_stimulus): RTLFS_E_STATE otherwise.
+ *
+ * Scratch: a file-scope device array of RTLFS_STATIC_SCRATCH_BYTES (64 MiB) inside the
+ * library, held by every GPU that loads the library until the process exits. A design
+ * needs 12 B per net + 8 B per node + 24 B per register of scratch per simultaneously
+ * simulated fault (faults run in waves that fit); a design whose single fault does not
+ * fit is rejected with RTLFS_E_ARG. Every call shares the array and leaves its contents
+ * behind; the call clears what must start at zero. Calls whose work overlaps on the GPU
+ * (other threads, other streams) race on the array: serialise them.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and keeps it; make that first call before any stream capture. The call enqueues on
+ * `stream` (a cudaStream_t; null = the legacy default stream), waits for the stream, and
+ * returns RTLFS_E_ARG if a fault's net, bit or stuck value is out of range (that fault's
+ * result carries detected = 254). */
+#define RTLFS_STATIC_SCRATCH_BYTES (64u << 20)
+int rtlfs_fault_sim_static(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults,
+                           uint32_t n_faults, rtlfs_result *results, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,8 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librtlfs.so")
-SOURCES = ["rtlfs_host.cu", "rtlfs_kernels.cu", "rtlfs_sched.cu"]
-HEADERS = [os.path.join(CSRC, "rtlfs_internal.h"), os.path.join(CSRC, "rtlfs_sched.h"), os.path.join(ROOT, "include", "rtlfs.h")]
+SOURCES = ["rtlfs_host.cu", "rtlfs_kernels.cu", "rtlfs_sched.cu", "rtlfs_static.cu"]
+HEADERS = [os.path.join(CSRC, "rtlfs_internal.h"), os.path.join(CSRC, "rtlfs_sched.h"), os.path.join(CSRC, "rtlfs_static.h"), os.path.join(ROOT, "include", "rtlfs.h")]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

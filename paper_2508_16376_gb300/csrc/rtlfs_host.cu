@@ -8,6 +8,7 @@
 #include "../../include/rtlfs.h"
 #include "rtlfs_internal.h"
 #include "rtlfs_sched.h"
+#include "rtlfs_static.h"
 
 #include <cuda_bf16.h>
 #include <deque>
@@ -1379,6 +1380,55 @@ int rtlfs_mlp_train(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, 
     CU(cudaMemcpyAsync(&lsum, ctx->d_loss.p, sizeof(float), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
     if (final_loss) *final_loss = lsum / (float)n;
+    return RTLFS_OK;
+}
+
+// Allocation-free variant of the plain form (see include/rtlfs.h): per-thread scratch in
+// the library's static device array, faults and results in the caller's device buffers.
+int rtlfs_fault_sim_static(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults,
+                           uint32_t n_faults, rtlfs_result *results, void *stream) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size()) return fail(ctx, RTLFS_E_ARG, "bad design id");
+    if (n_faults && (!faults || !results)) return fail(ctx, RTLFS_E_ARG, "null faults or results");
+    Design &D = *ctx->designs[design_id];
+    if (!D.has_stim || !D.trace_valid)
+        return fail(ctx, RTLFS_E_STATE, "the design's good trace is not current: call rtlfs_run or "
+                                        "rtlfs_good_outputs after the last rtlfs_set_stimulus");
+    if (!n_faults) return RTLFS_OK;
+    CU(cudaSetDevice(ctx->device));
+    void *arena_v = nullptr;
+    CU(static_scratch_address(ctx->device, &arena_v));
+    unsigned char *arena = (unsigned char *)arena_v;
+    StaticLayout L{};
+    L.sn = D.n_net;
+    L.snode = std::max<uint32_t>(D.N, 1);
+    L.sreg = std::max<uint32_t>(D.R, 1);
+    L.per_thread = ((size_t)12 * L.sn + (size_t)8 * L.snode + (size_t)24 * L.sreg + 15) & ~(size_t)15;
+    L.ext2int_off = 0;
+    L.err_off = ((size_t)4 * D.n_net + 7) & ~(size_t)7;
+    L.thread_off = (L.err_off + 8 + 255) & ~(size_t)255;
+    if (L.thread_off + L.per_thread > STATIC_SCRATCH_BYTES)
+        return fail(ctx, RTLFS_E_ARG, "design needs %zu bytes of scratch per fault; the static scratch "
+                                      "holds %zu bytes", L.thread_off + L.per_thread,
+                    (size_t)STATIC_SCRATCH_BYTES);
+    const uint32_t wave = (uint32_t)std::min<size_t>(n_faults, (STATIC_SCRATCH_BYTES - L.thread_off) / L.per_thread);
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(arena + L.ext2int_off, D.ext2int.data(), (size_t)4 * D.n_net,
+                       cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(arena + L.err_off, 0, 8, s));
+    for (uint32_t first = 0; first < n_faults; first += wave) {
+        const uint32_t cnt = std::min(wave, n_faults - first);
+        // value stamps and queued stamps must start at zero for every thread of the wave
+        CU(cudaMemsetAsync(arena + L.thread_off, 0, (size_t)cnt * L.per_thread, s));
+        CU(launch_plain_static(ctx->d_designs.p, design_id, faults, results, first, cnt, arena, L, s));
+    }
+    uint32_t err = 0;
+    CU(cudaMemcpyAsync(&err, arena + L.err_off, sizeof(err), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (err)
+        return fail(ctx, RTLFS_E_ARG, "a fault's net, bit or stuck value is out of range (its result "
+                                      "carries detected = 254)");
+    ctx->err.clear();
     return RTLFS_OK;
 }
 

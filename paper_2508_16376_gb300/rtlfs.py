@@ -85,6 +85,7 @@ EXPORTS = {
     "rtlfs_mlp_grad": ([V, V, V, ctypes.c_uint32, V, V], ctypes.c_int),
     "rtlfs_mlp_train": ([V, V, V, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                          ctypes.c_float, V], ctypes.c_int),
+    "rtlfs_fault_sim_static": ([V, ctypes.c_uint32, V, ctypes.c_uint32, V, V], ctypes.c_int),
 }
 MLP_PARAMS = 4609
 MLP_IN = 5
@@ -287,6 +288,15 @@ def rtlfs_mlp_train(ctx, X: np.ndarray, t: np.ndarray, epochs: int, batch: int, 
     _check(ctx, load_library().rtlfs_mlp_train(ctx, _ptr(X), _ptr(t), X.shape[0], epochs, batch,
                                                lr, ctypes.byref(loss)))
     return float(loss.value)
+
+
+def rtlfs_fault_sim_static(ctx, design_id: int, faults_dev_ptr: int, n_faults: int,
+                           results_dev_ptr: int, stream_ptr: int = 0) -> int:
+    """Allocation-free plain-form simulation on caller-owned device buffers (raw device
+    pointers: faults as FAULT_DTYPE records, results as RESULT_DTYPE records). Returns the
+    status code; raises nothing so that callers can inspect it."""
+    return load_library().rtlfs_fault_sim_static(ctx, design_id, faults_dev_ptr or None, n_faults,
+                                                  results_dev_ptr or None, stream_ptr or None)
 
 
 # ---- convenience wrapper ----------------------------------------------------------------
