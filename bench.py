@@ -35,6 +35,11 @@ WORKLOAD = dict(workload="medium datapath+FSM RTL design, stuck-at campaign",
                 fault_seed=202)
 
 
+# Campaign options the bench times: windows of 256 cycles (good trace, light and heavy
+# kernels overlapped on three streams), default light capacity, one warp per heavy fault.
+DEFAULT_OPTS = {"window": 256}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -158,6 +163,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--opts", default=json.dumps(DEFAULT_OPTS),
+                    help="rtlfs_run options as JSON (default: the tuned campaign options)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -187,16 +194,16 @@ def main():
 
     sim = Simulator(local)
     sim.add(d, stim, faults)
-    opts = rtlfs.make_opts()
+    run_opts = json.loads(args.opts)
     # warm-up (also allocates every buffer)
     for _ in range(args.warmup):
-        sim.run(**{})
+        sim.run(**run_opts)
     barrier()
     stats = []
     with Clocks(local) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            sim.run()
+            sim.run(**run_opts)
             stats.append(sim.stats())
         barrier()
         wall = time.perf_counter() - t0
@@ -221,7 +228,7 @@ def main():
         t1 = time.perf_counter()
         rtlfs.rtlfs_set_stimulus(sim.ctx, 0, stim)
         rtlfs.rtlfs_set_faults(sim.ctx, 0, fa)
-        sim.run()
+        sim.run(**run_opts)
         te.append(time.perf_counter() - t1)
     barrier()
     e2e_s = float(np.mean(te))
@@ -237,7 +244,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": dict(WORKLOAD, l2="good trace 2 x 1.77 GB rewritten every step (> L2)",
-                           parallelism=f"fault shards x{ws}"),
+                           parallelism=f"fault shards x{ws}", run_opts=run_opts),
             "wall_ms_per_step": 1000 * wall / args.steps,
             "campaign": {k: last[k] for k in ("good_ms", "prep_ms", "light_ms", "heavy_ms",
                                                "promoted", "heavy_initial", "node_evals",

@@ -112,6 +112,7 @@ struct rtlfs_ctx {
     DBuf<uint32_t> w_st_r, w_live0, w_live1, w_cnt32, w_pool_r0, w_pool_r1;
     DBuf<uint64_t> w_st_v, w_pool_v0, w_pool_v1;
     DBuf<unsigned long long> w_cnt64;
+    DBuf<uint64_t> d_act;              // activation bitplane [F][ceil(Tmax/64)]
     DBuf<HeavyCarry> w_carry0, w_carry1;
     uint64_t w_pool_cap = 0;
     cudaEvent_t ev_wg = nullptr, ev_wl = nullptr;
@@ -859,6 +860,15 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         ci[3] = 0;
     }
     const bool timed_windows = W && !o.use_graph;
+    // Activation bitplane: built after the good trace (per window when windows are whole
+    // multiples of 64 cycles); otherwise the kernels scan the good trace.
+    const bool use_act = F > 0 && (W == 0 || W % 64 == 0);
+    const uint32_t act_stride = (Tmax + 63) / 64;
+    if (use_act) {
+        CU(ctx->d_act.reserve((size_t)F * act_stride));
+        f.act = ctx->d_act.p;
+        f.act_stride = act_stride;
+    }
 
     // Windowed stream work (good trace on s_good, light on s_main, heavy on s_heavy).
     auto enqueue_windowed = [&]() -> int {
@@ -891,6 +901,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                                  ctx->d_err.p, ctx->s_good, t0, t1));
             CU(launch_transpose_window(ctx->d_designs.p, (uint32_t)ctx->designs.size(), max_net, t0, t1, ctx->s_good));
             launches += 3;
+            if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, t0, t1, ctx->s_good)); ++launches; }
             if (w == 0) CU(cudaEventRecord(ev[1], ctx->s_good));
             CU(cudaEventRecord(ctx->ev_wg, ctx->s_good));
             // light kernel of the window (after the scheduler for the first one)
@@ -914,6 +925,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             WinLight wl{};
             wl.live_in = w == 0 ? ctx->d_order.p + n_heavy : (w & 1 ? ctx->w_live0.p : ctx->w_live1.p);
             wl.n_live_in = w == 0 ? n_light0 : c32 + (w - 1);
+            wl.reverse = w > 0;
             wl.live_out = (w & 1) ? ctx->w_live1.p : ctx->w_live0.p;
             wl.n_live_out = c32 + w;
             wl.head = c64 + nw + w;
@@ -992,6 +1004,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         int r2 = launch_good(ctx);
         if (r2 != RTLFS_OK) return r2;
         launches += 2 + (uint32_t)ctx->designs.size();
+        if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, 0, Tmax, ctx->s_main)); ++launches; }
         CU(cudaEventRecord(ev[1], ctx->s_main));
         if (dev_sched) {
             CU(launch_features(ctx->d_designs.p, f, ctx->d_static_ptrs.p, ctx->d_X.p, ctx->d_heur.p, ctx->s_main));
@@ -1043,7 +1056,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                               ctx->d_wb.p, ctx->d_static_ptrs.p, ctx->w_st_nreg.p, ctx->w_st_r.p,
                               ctx->w_st_v.p, ctx->w_live0.p, ctx->w_live1.p, ctx->w_cnt32.p, ctx->w_cnt64.p,
                               ctx->w_carry0.p, ctx->w_carry1.p, ctx->w_pool_r0.p, ctx->w_pool_r1.p,
-                              ctx->w_pool_v0.p, ctx->w_pool_v1.p};
+                              ctx->w_pool_v0.p, ctx->w_pool_v1.p, ctx->d_act.p};
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
@@ -1111,6 +1124,10 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     }
     st.promoted = cnts[1];
     st.heavy_initial = cnts[0];
+    if (W) {   // the windowed form reports the promotion list's total (initial + promoted)
+        st.heavy_initial = n_heavy;
+        st.promoted = cnts[0] - n_heavy;
+    }
     st.n_launches = launches;
     st.light_evals = heads[4];
     st.light_fault_cycles = heads[5];

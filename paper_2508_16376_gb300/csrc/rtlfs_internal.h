@@ -72,6 +72,11 @@ struct DevFaults {
     int32_t  *res_port;
     uint8_t  *res_det;
     uint64_t *load;             // node evaluations, summed over simulated cycles
+    // Activation bitplane (optional, null = scan the good trace): bit (t mod 64) of
+    // act[fault * act_stride + t / 64] is set when the site bit's good value at cycle t
+    // differs from the stuck value, i.e. when the fault makes the machines differ by itself.
+    const uint64_t *act;
+    uint32_t act_stride;
 };
 
 // Light-lane capacities (per fault, per cycle): register diffs, net diffs, pending nodes.
@@ -130,6 +135,7 @@ struct HeavyCarry {
 
 struct WinLight {
     const uint32_t *live_in;      // fault ids alive at t0
+    uint32_t reverse;             // 1: take live_in back to front (survivor lists)
     const uint32_t *n_live_in;    // device count of live_in
     uint32_t *live_out;           // survivors at t1 (appended, order unspecified)
     uint32_t *n_live_out;
@@ -177,6 +183,10 @@ cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design
                               uint32_t max_chunks, bool use_smem, uint32_t *err,
                               cudaStream_t stream, uint32_t t_begin = 0,
                               uint32_t t_end = 0xFFFFFFFFu);
+// Activation bitplane of every fault for cycles [t0, t1) (t0 a multiple of 64; t1 a
+// multiple of 64 or the design's last cycle).
+cudaError_t launch_activation(const DevDesign *d_designs, DevFaults f, uint64_t *act,
+                              uint32_t t0, uint32_t t1, cudaStream_t stream);
 // rows -> gcol for cycles [t0, t1) of all n_designs designs (one launch).
 cudaError_t launch_transpose_window(const DevDesign *d_designs, uint32_t n_designs,
                                     uint32_t max_net, uint32_t t0, uint32_t t1,

@@ -233,6 +233,41 @@ __global__ void transpose_window_kernel(const DevDesign *__restrict__ designs, u
     }
 }
 
+// Activation bitplane: one warp per fault reads 64 consecutive cycles of the site column
+// (two coalesced 256-byte rows) and writes one 64-bit word per 64 cycles.
+__global__ void activation_kernel(const DevDesign *__restrict__ designs, DevFaults f, uint64_t *act,
+                                  uint32_t t0, uint32_t t1) {
+    const uint32_t fid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (fid >= f.F) return;
+    const DevDesign &D = designs[f.design[fid]];
+    const uint32_t T = D.T, te = min(t1, T);
+    const uint32_t site = f.site[fid], bit = f.bit[fid];
+    const uint64_t sv = f.val[fid];
+    const uint64_t *col = D.gcol + (size_t)site * T;
+    uint64_t *out = act + (size_t)fid * f.act_stride;
+    for (uint32_t tw = t0; tw < te; tw += 64) {
+        const uint32_t ta = tw + lane, tb = tw + 32 + lane;
+        const bool a = ta < te && ((__ldg(col + ta) >> bit) & 1ull) != sv;
+        const bool b = tb < te && ((__ldg(col + tb) >> bit) & 1ull) != sv;
+        const uint32_t lo = __ballot_sync(0xFFFFFFFFu, a), hi = __ballot_sync(0xFFFFFFFFu, b);
+        if (lane == 0) out[tw >> 6] = ((uint64_t)hi << 32) | lo;
+    }
+}
+
+// First cycle in [t, tend) where the fault is active by itself, or tend.
+__device__ __forceinline__ uint32_t next_active(const uint64_t *__restrict__ fact, uint32_t t, uint32_t tend) {
+    while (t < tend) {
+        const uint64_t w = __ldg(fact + (t >> 6)) >> (t & 63u);
+        if (w) {
+            const uint32_t a = t + (uint32_t)(__ffsll((long long)w) - 1);
+            return a < tend ? a : tend;
+        }
+        t = (t | 63u) + 1;
+    }
+    return tend;
+}
+
 // ===================================================================================
 // Light kernel: one lane per fault, persistent, lanes take faults from a global queue
 // (atomic counter) as they finish -- dynamic balancing of the many low-load faults.
@@ -292,19 +327,23 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
         for (;;) {
             if (nreg == 0) {
                 // Skip quiescent cycles: nothing differs unless the site bit is activated.
-                // Four cycles per step, loads issued together.
+                // With the activation bitplane, 64 cycles per load; else four cycles per step.
                 const uint64_t want = sv ? bm : 0ull;   // site bit equal to the stuck value: quiescent
-                while (t + 4 <= T) {
-                    const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
-                    const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
-                    if ((g0 & bm) != want) break;
-                    if ((g1 & bm) != want) { t += 1; break; }
-                    if ((g2 & bm) != want) { t += 2; break; }
-                    if ((g3 & bm) != want) { t += 3; break; }
-                    t += 4;
-                }
-                if (t + 4 > T) {
-                    while (t < T && (__ldg(scol + t) & bm) == want) ++t;
+                if (f.act) {
+                    t = next_active(f.act + (size_t)fid * f.act_stride, t, T);
+                } else {
+                    while (t + 4 <= T) {
+                        const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
+                        const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
+                        if ((g0 & bm) != want) break;
+                        if ((g1 & bm) != want) { t += 1; break; }
+                        if ((g2 & bm) != want) { t += 2; break; }
+                        if ((g3 & bm) != want) { t += 3; break; }
+                        t += 4;
+                    }
+                    if (t + 4 > T) {
+                        while (t < T && (__ldg(scol + t) & bm) == want) ++t;
+                    }
                 }
                 if (t >= T) break;
             }
@@ -492,6 +531,9 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
     // the range ring holds 8-byte entries: start it on an even word (heavy_smem_bytes agrees)
     const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + 1) & ~(size_t)1;
     uint2 *frange = reinterpret_cast<uint2 *>(hsm + fr_words);   // [HEAVY_FRANGE]
+    // one bit per level that has dirty nodes: the level loop visits only those
+    unsigned long long *lvm = reinterpret_cast<unsigned long long *>(frange + HEAVY_FRANGE);
+    const uint32_t nlw = (S.max_levels + 63) / 64;
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
     __shared__ unsigned long long s_load;
@@ -504,6 +546,7 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
     for (uint32_t i = tid; i < nwn; i += B) bm[i] = 0;
     for (uint32_t i = tid; i < S.max_levels; i += B) cnt[i] = 0;
     for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
+    for (uint32_t i = tid; i < nlw; i += B) lvm[i] = 0;
     if (tid == 0) s_nfr = 0;
     __syncthreads();
 
@@ -545,7 +588,7 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                 const uint32_t lv = __ldg(fo_lvl + e);
                 const uint32_t b1 = 1u << (c & 31u);
                 const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
-                if (!(o2 & b1)) atomicAdd(&cnt[lv], 1u);
+                if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
             }
         };
         // Ranges live in a ring indexed by a per-cycle append counter s_nfr; fr_begin (the
@@ -564,7 +607,9 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
 
         for (;;) {
             if (nreg == 0) {
-                if (warp == 0) {
+                if (warp == 0 && f.act) {
+                    if (lane == 0) s_t = next_active(f.act + (size_t)fid * f.act_stride, t, T);
+                } else if (warp == 0) {
                     uint32_t found = T;
                     for (uint32_t tt = t; tt < T; tt += 32) {
                         const uint32_t u = tt + lane;
@@ -639,15 +684,22 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                     const uint32_t c = site - IR;
                     const uint32_t b1 = 1u << (c & 31u);
                     const uint32_t old = atomicOr(&bm[c >> 5], b1);
-                    if (!(old & b1)) atomicAdd(&cnt[__ldg(D.node_level + c)], 1u);
+                    const uint32_t lv = __ldg(D.node_level + c);
+                    if (!(old & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
                 }
             }
             __syncthreads();
             expand();
             __syncthreads();
             uint32_t my_load = 0;
-            for (uint32_t L = 0; L < NL; ++L) {
-                if (cnt[L] == 0) continue;
+            for (uint32_t L = 0;;) {
+                // next level with dirty nodes (bits are only ever set above the current level)
+                uint32_t lw = L >> 6;
+                unsigned long long m = lw < nlw ? lvm[lw] & (~0ull << (L & 63u)) : 0ull;
+                while (!m && ++lw < nlw) m = lvm[lw];
+                if (!m) break;
+                L = (lw << 6) + (uint32_t)(__ffsll((long long)m) - 1);
+                if (L >= NL) break;
                 const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
                 const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
                 for (uint32_t w = w0 + tid; w <= w1; w += B) {
@@ -682,7 +734,12 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                     expand();
                     __syncthreads();
                 }
-                if (tid == 0) cnt[L] = 0;
+                if (tid == 0) {
+                    cnt[L] = 0;
+                    atomicAnd(&lvm[L >> 6], ~(1ull << (L & 63u)));
+                }
+                __syncthreads();
+                ++L;
             }
             if (my_load) atomicAdd(&s_load, (unsigned long long)my_load);
             __syncthreads();
@@ -743,7 +800,9 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
     for (;;) {
         const unsigned long long qi = atomicAdd(q.head, 1ull);
         if (qi >= n_live) break;
-        const uint32_t fid = q.live_in[qi];
+        // Survivors were appended in the order they finished the last window, slowest last:
+        // take them back to front so the slowest start first (longest processing time first).
+        const uint32_t fid = q.live_in[q.reverse ? n_live - 1 - (uint32_t)qi : (uint32_t)qi];
         const DevDesign &D = designs[f.design[fid]];
         const uint32_t I = D.I, IR = D.I + D.R, T = D.T;
         const uint32_t tend = min(q.t1, T);     // this window ends at tend
@@ -771,19 +830,23 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
         for (;;) {
             if (nreg == 0) {
                 // Skip quiescent cycles: nothing differs unless the site bit is activated.
-                // Four cycles per step, loads issued together.
+                // With the activation bitplane, 64 cycles per load; else four cycles per step.
                 const uint64_t want = sv ? bm : 0ull;   // site bit equal to the stuck value: quiescent
-                while (t + 4 <= tend) {
-                    const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
-                    const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
-                    if ((g0 & bm) != want) break;
-                    if ((g1 & bm) != want) { t += 1; break; }
-                    if ((g2 & bm) != want) { t += 2; break; }
-                    if ((g3 & bm) != want) { t += 3; break; }
-                    t += 4;
-                }
-                if (t + 4 > tend) {
-                    while (t < tend && (__ldg(scol + t) & bm) == want) ++t;
+                if (f.act) {
+                    t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
+                } else {
+                    while (t + 4 <= tend) {
+                        const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
+                        const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
+                        if ((g0 & bm) != want) break;
+                        if ((g1 & bm) != want) { t += 1; break; }
+                        if ((g2 & bm) != want) { t += 2; break; }
+                        if ((g3 & bm) != want) { t += 3; break; }
+                        t += 4;
+                    }
+                    if (t + 4 > tend) {
+                        while (t < tend && (__ldg(scol + t) & bm) == want) ++t;
+                    }
                 }
                 if (t >= tend) break;
             }
@@ -978,6 +1041,9 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
     // the range ring holds 8-byte entries: start it on an even word (heavy_smem_bytes agrees)
     const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + 1) & ~(size_t)1;
     uint2 *frange = reinterpret_cast<uint2 *>(hsm + fr_words);   // [HEAVY_FRANGE]
+    // one bit per level that has dirty nodes: the level loop visits only those
+    unsigned long long *lvm = reinterpret_cast<unsigned long long *>(frange + HEAVY_FRANGE);
+    const uint32_t nlw = (S.max_levels + 63) / 64;
     __shared__ unsigned long long s_item, s_off;
     __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
     __shared__ unsigned long long s_load;
@@ -990,6 +1056,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
     for (uint32_t i = tid; i < nwn; i += B) bm[i] = 0;
     for (uint32_t i = tid; i < S.max_levels; i += B) cnt[i] = 0;
     for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
+    for (uint32_t i = tid; i < nlw; i += B) lvm[i] = 0;
     if (tid == 0) s_nfr = 0;
     __syncthreads();
 
@@ -1001,7 +1068,8 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         const unsigned long long idx = s_item;
         if (idx >= n_items) break;
         const bool carried = idx < n_carry;
-        const HeavyCarry cin = carried ? q.carry_in[idx] : HeavyCarry{0, 0, 0};
+        // carried faults back to front: the slowest of the last window first
+        const HeavyCarry cin = carried ? q.carry_in[n_carry - 1 - (uint32_t)idx] : HeavyCarry{0, 0, 0};
         const HeavyItem &it = q.prom[pb + (carried ? 0 : idx - n_carry)];
         const uint32_t fid = carried ? cin.fault : it.fault;
         const DevDesign &D = designs[f.design[fid]];
@@ -1035,7 +1103,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
                 const uint32_t lv = __ldg(fo_lvl + e);
                 const uint32_t b1 = 1u << (c & 31u);
                 const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
-                if (!(o2 & b1)) atomicAdd(&cnt[lv], 1u);
+                if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
             }
         };
         // Ranges live in a ring indexed by a per-cycle append counter s_nfr; fr_begin (the
@@ -1054,7 +1122,9 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
 
         for (;;) {
             if (nreg == 0) {
-                if (warp == 0) {
+                if (warp == 0 && f.act) {
+                    if (lane == 0) s_t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
+                } else if (warp == 0) {
                     uint32_t found = tend;
                     for (uint32_t tt = t; tt < tend; tt += 32) {
                         const uint32_t u = tt + lane;
@@ -1129,15 +1199,22 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
                     const uint32_t c = site - IR;
                     const uint32_t b1 = 1u << (c & 31u);
                     const uint32_t old = atomicOr(&bm[c >> 5], b1);
-                    if (!(old & b1)) atomicAdd(&cnt[__ldg(D.node_level + c)], 1u);
+                    const uint32_t lv = __ldg(D.node_level + c);
+                    if (!(old & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
                 }
             }
             __syncthreads();
             expand();
             __syncthreads();
             uint32_t my_load = 0;
-            for (uint32_t L = 0; L < NL; ++L) {
-                if (cnt[L] == 0) continue;
+            for (uint32_t L = 0;;) {
+                // next level with dirty nodes (bits are only ever set above the current level)
+                uint32_t lw = L >> 6;
+                unsigned long long m = lw < nlw ? lvm[lw] & (~0ull << (L & 63u)) : 0ull;
+                while (!m && ++lw < nlw) m = lvm[lw];
+                if (!m) break;
+                L = (lw << 6) + (uint32_t)(__ffsll((long long)m) - 1);
+                if (L >= NL) break;
                 const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
                 const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
                 for (uint32_t w = w0 + tid; w <= w1; w += B) {
@@ -1172,7 +1249,12 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
                     expand();
                     __syncthreads();
                 }
-                if (tid == 0) cnt[L] = 0;
+                if (tid == 0) {
+                    cnt[L] = 0;
+                    atomicAnd(&lvm[L >> 6], ~(1ull << (L & 63u)));
+                }
+                __syncthreads();
+                ++L;
             }
             if (my_load) atomicAdd(&s_load, (unsigned long long)my_load);
             __syncthreads();
@@ -1394,6 +1476,13 @@ cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_ne
     return cudaGetLastError();
 }
 
+cudaError_t launch_activation(const DevDesign *d_designs, DevFaults f, uint64_t *act, uint32_t t0,
+                              uint32_t t1, cudaStream_t stream) {
+    if (!f.F || t1 <= t0) return cudaSuccess;
+    activation_kernel<<<(f.F + 7) / 8, 256, 0, stream>>>(d_designs, f, act, t0, t1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_transpose_window(const DevDesign *d_designs, uint32_t n_designs, uint32_t max_net,
                                     uint32_t t0, uint32_t t1, cudaStream_t stream) {
     if (!n_designs || t1 <= t0) return cudaSuccess;
@@ -1458,7 +1547,8 @@ cudaError_t launch_light_window(const DevDesign *d_designs, DevFaults f, WinLigh
 size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net) {
     size_t words = (size_t)(max_node + 31) / 32 + max_levels + (max_net + 31) / 32 + HEAVY_DLIST;
     words = (words + 1) & ~(size_t)1;   // 8-byte alignment of the range list
-    return words * sizeof(uint32_t) + HEAVY_FRANGE * sizeof(uint2);
+    return words * sizeof(uint32_t) + HEAVY_FRANGE * sizeof(uint2) +
+           (size_t)((max_levels + 63) / 64) * sizeof(unsigned long long);
 }
 
 int heavy_max_blocks_per_sm(int block, size_t smem) {
