@@ -63,7 +63,7 @@ struct Design {
     std::vector<uint32_t> lvl_start;
     std::vector<uint16_t> node_level;
     std::vector<uint8_t> net_w;
-    std::vector<uint32_t> fo_off, fo_idx, dreg_off, dreg_idx, reg_d, outport, out_net;
+    std::vector<uint32_t> fo_off, fo_idx, dreg_off, dreg_idx, dreg_rec, reg_d, outport, out_net;
     std::vector<uint4> netinfo;
     std::vector<uint2> chunks;
     std::vector<float> cone;          // static fan-out cone size estimate per net (log2 scale)
@@ -71,8 +71,8 @@ struct Design {
     DBuf<float> d_net_static;
     DBuf<uint4> d_desc, d_netinfo;
     DBuf<uint2> d_chunks;
-    DBuf<uint32_t> d_lvl_start, d_fo_off, d_fo_idx, d_dreg_off, d_dreg_idx, d_reg_d, d_outport,
-        d_out_net;
+    DBuf<uint32_t> d_lvl_start, d_fo_off, d_fo_idx, d_dreg_off, d_dreg_idx, d_dreg_rec, d_reg_d,
+        d_outport, d_out_net;
     DBuf<uint16_t> d_node_level, d_fo_lvl;
     std::vector<uint16_t> fo_lvl;
     DBuf<uint8_t> d_net_w;
@@ -342,6 +342,10 @@ int build_design(rtlfs_ctx *ctx, Design &D, const rtlfs_node *nodes, uint32_t N,
         std::vector<uint32_t> f2(D.dreg_off.begin(), D.dreg_off.end() - 1);
         for (uint32_t r = 0; r < R; ++r) D.dreg_idx[f2[D.reg_d[r]]++] = r;
     }
+    if (R >= (1u << 25)) return fail(ctx, RTLFS_E_ARG, "more than 2^25 registers");
+    D.dreg_rec.resize(R);
+    for (uint32_t e = 0; e < R; ++e)
+        D.dreg_rec[e] = D.dreg_idx[e] | ((uint32_t)wext[I + D.dreg_idx[e]] << 25);
     // Outputs.
     D.out_net.resize(O);
     D.outport.assign(n_net, NO_PORT);
@@ -429,6 +433,7 @@ int upload_design(rtlfs_ctx *ctx, Design &D) {
     CU(D.d_fo_lvl.upload(D.fo_lvl));
     CU(D.d_dreg_off.upload(D.dreg_off));
     CU(D.d_dreg_idx.upload(D.dreg_idx));
+    CU(D.d_dreg_rec.upload(D.dreg_rec));
     CU(D.d_reg_d.upload(D.reg_d));
     CU(D.d_outport.upload(D.outport));
     CU(D.d_out_net.upload(D.out_net));
@@ -443,7 +448,7 @@ DevDesign dev_view(const Design &D) {
     v.netinfo = D.d_netinfo.p; v.chunks = D.d_chunks.p;
     v.desc = D.d_desc.p; v.lvl_start = D.d_lvl_start.p; v.node_level = D.d_node_level.p;
     v.net_w = D.d_net_w.p; v.fo_off = D.d_fo_off.p; v.fo_idx = D.d_fo_idx.p; v.fo_lvl = D.d_fo_lvl.p;
-    v.dreg_off = D.d_dreg_off.p; v.dreg_idx = D.d_dreg_idx.p; v.reg_d = D.d_reg_d.p;
+    v.dreg_off = D.d_dreg_off.p; v.dreg_idx = D.d_dreg_idx.p; v.dreg_rec = D.d_dreg_rec.p; v.reg_d = D.d_reg_d.p;
     v.outport = D.d_outport.p; v.out_net = D.d_out_net.p; v.stim = D.d_stim.p;
     v.rows = D.d_rows.p; v.gcol = D.d_gcol.p;
     return v;
@@ -479,6 +484,9 @@ int prepare_good(rtlfs_ctx *ctx) {
     CU(ctx->d_list_smem.upload(l_smem));
     CU(ctx->d_list_glob.upload(l_glob));
     if (good_smem_bytes(false, 0, 0, max_ch_g) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
+    for (Design *D : ctx->designs)   // chunk instances of one good-trace launch fit 32 bits
+        if ((uint64_t)D->T * D->chunks.size() >= (1ull << 32))
+            return fail(ctx, RTLFS_E_ARG, "cycles x chunks too large for one launch: use windows");
     CU(ctx->d_err.reserve(1));
     ctx->gl = {(uint32_t)l_smem.size(), (uint32_t)l_glob.size(), max_net_s, max_reg_s, max_ch_s, max_ch_g};
     return RTLFS_OK;

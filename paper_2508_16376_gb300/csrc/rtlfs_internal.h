@@ -53,6 +53,7 @@ struct DevDesign {
     const uint16_t *fo_lvl;     // [n_fo] level of each consumer
     const uint32_t *dreg_off;   // [n_net + 1] registers latching each net
     const uint32_t *dreg_idx;   // [n_dreg]
+    const uint32_t *dreg_rec;   // [n_dreg] register index | register width << 25
     const uint32_t *reg_d;      // [R] internal id of each register's D net
     const uint32_t *outport;    // [n_net] lowest output port observing the net, or NO_PORT
     const uint32_t *out_net;    // [O] internal id observed by each port
@@ -109,10 +110,10 @@ struct Queues {
 
 // Words of the heavy kernel's net bitmap remembered for clearing; beyond this many the
 // whole bitmap is cleared at the end of the cycle.
-constexpr uint32_t HEAVY_DLIST = 512;
+constexpr uint32_t HEAVY_DLIST = 128;
 // Fan-out ranges a heavy CTA collects per level before marking consumers together; a
 // range beyond this many is marked by the thread that kept the net.
-constexpr uint32_t HEAVY_FRANGE = 256;
+constexpr uint32_t HEAVY_FRANGE = 64;
 // Fan-out lists up to this long are marked by the thread that kept the net.
 constexpr uint32_t HEAVY_INLINE_FANOUT = 16;
 

@@ -131,17 +131,19 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
     }
     __syncthreads();
 
-    const uint64_t total = (uint64_t)(T - t_begin) * NC;   // chunk instances of this launch
+    // chunk instances of this launch (the host keeps windows small enough for 32 bits)
+    const uint32_t total = (T - t_begin) * NC;
     uint32_t cf = 0;                           // chunk index of the next issue (wraps)
-    auto issue = [&](uint64_t k) {             // thread 0: chunk instance k into its buffer
+    auto issue = [&](uint32_t buf) {           // thread 0: the next chunk instance into buf
         const uint2 b = ch[cf];
         const uint32_t n = (b.y & 0x7FFFFFFFu) - b.x;
-        tma_issue(mbar + (k % GOOD_NBUF), stage + (k % GOOD_NBUF) * GOOD_BLOCK, D.desc + b.x, n * 16u);
+        tma_issue(mbar + buf, stage + buf * GOOD_BLOCK, D.desc + b.x, n * 16u);
         cf = cf + 1 == NC ? 0 : cf + 1;
     };
     if (tid == 0)
-        for (uint64_t k = 0; k < GOOD_NBUF && k < total; ++k) issue(k);
-    uint64_t kc = 0;                           // chunk instance being consumed
+        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && k < total; ++k) issue(k);
+    uint32_t kc = 0;                           // chunk instance being consumed
+    uint32_t buf = 0, par = 0;                 // its buffer and the parity of that buffer's phase
     uint64_t s_next = (tid < I) ? __ldg(D.stim + (size_t)t_begin * I + tid) : 0ull;
     bool failed = false;
 
@@ -161,10 +163,10 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
         __syncthreads();
         for (uint32_t c = 0; c < NC; ++c, ++kc) {
             const uint2 b = ch[c];
-            const uint32_t buf = (uint32_t)(kc % GOOD_NBUF);
-            const bool staged = mbar_wait(mbar + buf, (uint32_t)((kc / GOOD_NBUF) & 1));
             const uint32_t n = b.x + tid;
-            if (staged && n < (b.y & 0x7FFFFFFFu)) {
+            const bool mine = n < (b.y & 0x7FFFFFFFu);   // thread 0 always owns a node
+            const bool staged = mine ? mbar_wait(mbar + buf, par) : true;
+            if (staged && mine) {
                 const uint4 d0 = stage[buf * GOOD_BLOCK + tid];
                 const uint32_t op = meta_op(d0.w);
                 const int no = n_operands(op);
@@ -178,7 +180,8 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
             }
             // every thread is done with this buffer (and every wait succeeded): refill it
             if (!__syncthreads_and(staged)) { failed = true; break; }
-            if (tid == 0 && kc + GOOD_NBUF < total) issue(kc + GOOD_NBUF);
+            if (tid == 0 && kc + GOOD_NBUF < total) issue(buf);
+            if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
         }
         if (failed) break;
         if (USE_SMEM) {
@@ -192,8 +195,10 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
         // a staging wait ran out: report it, give the copies still in flight a bounded
         // chance to land, and leave
         atomicOr(err, 1u);
-        for (uint64_t k = kc; k < kc + GOOD_NBUF && k < total; ++k)
-            mbar_wait(mbar + (k % GOOD_NBUF), (uint32_t)((k / GOOD_NBUF) & 1));
+        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && kc + k < total; ++k) {
+            mbar_wait(mbar + buf, par);
+            if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
+        }
     }
 }
 
@@ -312,6 +317,8 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
         const uint4 *__restrict__ netinfo = D.netinfo;
         const uint4 *__restrict__ desc = D.desc;
         const uint32_t *__restrict__ fo_idx = D.fo_idx;
+        const uint32_t *__restrict__ dreg_off = D.dreg_off;
+        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
         const uint32_t site = f.site[fid];
         const uint32_t bit = f.bit[fid];
         const bool sv = f.val[fid] != 0;
@@ -407,10 +414,11 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
                 }
                 uint32_t nr = ni_nreg(ni.w);
                 if (nr) {
-                    if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                    if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
                     for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                        const uint32_t r = __ldg(D.dreg_idx + e);
-                        const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                        const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+                        const uint32_t r = rec & 0x1FFFFFFu;
+                        const uint64_t wm = wmask(rec >> 25);
                         const uint64_t qv = v & wm;
                         if (qv != (g & wm)) {
                             if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
@@ -564,6 +572,8 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         const uint4 *__restrict__ netinfo = D.netinfo;
         const uint32_t *__restrict__ fo_idx = D.fo_idx;
         const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
+        const uint32_t *__restrict__ dreg_off = D.dreg_off;
+        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
         const uint32_t site = f.site[fid];
         const uint32_t bit = f.bit[fid];
         const bool sv = f.val[fid] != 0;
@@ -648,10 +658,11 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
                     mark_range(ni.x, ni.y, 0, 1);
                 }
                 uint32_t nr = ni_nreg(ni.w);
-                if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
                 for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                    const uint32_t r = __ldg(D.dreg_idx + e);
-                    const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                    const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+                    const uint32_t r = rec & 0x1FFFFFFu;
+                    const uint64_t wm = wmask(rec >> 25);
                     const uint64_t qv = v & wm;
                     if (qv != (g & wm)) {
                         const uint32_t k = atomicAdd(&s_nreg_new, 1u);
@@ -810,6 +821,8 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
         const uint4 *__restrict__ netinfo = D.netinfo;
         const uint4 *__restrict__ desc = D.desc;
         const uint32_t *__restrict__ fo_idx = D.fo_idx;
+        const uint32_t *__restrict__ dreg_off = D.dreg_off;
+        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
         const uint32_t site = f.site[fid];
         const uint32_t bit = f.bit[fid];
         const bool sv = f.val[fid] != 0;
@@ -910,10 +923,11 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
                 }
                 uint32_t nr = ni_nreg(ni.w);
                 if (nr) {
-                    if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                    if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
                     for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                        const uint32_t r = __ldg(D.dreg_idx + e);
-                        const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                        const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+                        const uint32_t r = rec & 0x1FFFFFFu;
+                        const uint64_t wm = wmask(rec >> 25);
                         const uint64_t qv = v & wm;
                         if (qv != (g & wm)) {
                             if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
@@ -1079,6 +1093,8 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         const uint4 *__restrict__ netinfo = D.netinfo;
         const uint32_t *__restrict__ fo_idx = D.fo_idx;
         const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
+        const uint32_t *__restrict__ dreg_off = D.dreg_off;
+        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
         const uint32_t site = f.site[fid];
         const uint32_t bit = f.bit[fid];
         const bool sv = f.val[fid] != 0;
@@ -1163,10 +1179,11 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
                     mark_range(ni.x, ni.y, 0, 1);
                 }
                 uint32_t nr = ni_nreg(ni.w);
-                if (nr == 255u) nr = __ldg(D.dreg_off + net + 1) - ni.z;
+                if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
                 for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                    const uint32_t r = __ldg(D.dreg_idx + e);
-                    const uint64_t wm = wmask(__ldg(D.net_w + I + r));
+                    const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+                    const uint32_t r = rec & 0x1FFFFFFu;
+                    const uint64_t wm = wmask(rec >> 25);
                     const uint64_t qv = v & wm;
                     if (qv != (g & wm)) {
                         const uint32_t k = atomicAdd(&s_nreg_new, 1u);
