@@ -111,6 +111,9 @@ struct Queues {
 // Words of the heavy kernel's net bitmap remembered for clearing; beyond this many the
 // whole bitmap is cleared at the end of the cycle.
 constexpr uint32_t HEAVY_DLIST = 128;
+// Dirty nodes of one level a heavy CTA gathers into a list and splits over its threads;
+// a level with more is walked word by word.
+constexpr uint32_t HEAVY_NLIST = 256;
 // Fan-out ranges a heavy CTA collects per level before marking consumers together; a
 // range beyond this many is marked by the thread that kept the net.
 constexpr uint32_t HEAVY_FRANGE = 64;

@@ -521,267 +521,464 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
 // Heavy kernel: one CTA per fault (by default a single warp). Shared memory holds a bitmap
 // over the nodes (dirty: some operand differs), the number of dirty nodes per level (so an
 // empty level costs one shared read), a bitmap over the nets (differs this cycle) and a
-// list of fan-out ranges to expand. Differing values live in per-slot global scratch.
-// Each level runs in two phases: (1) the dirty nodes of the level are evaluated in
-// parallel -- the fault's bad gates split over the threads -- and a kept net marks its
-// consumers itself when it has few, or appends its fan-out range when it has many; (2)
-// all threads mark the consumers of the long ranges together, so a control net with
-// thousands of readers costs a few passes instead of one thread's loop.
+// ring of fan-out ranges to expand. Differing values live in per-slot global scratch.
+// Each level runs in up to three phases: (0) the level's dirty nodes are gathered from the
+// bitmap into a shared list, so they split evenly over the threads however they cluster
+// in the bitmap's words; (1) the threads evaluate them, and a kept net marks its consumers
+// itself when it has few -- a list of at most HEAVY_PREFETCH is fetched beside the
+// operands, so marking it waits on no further load -- or appends its fan-out range to the
+// ring when it has many; (2) all threads mark the consumers of the long ranges together,
+// so a control net with thousands of readers costs a few passes instead of one thread's
+// loop. The two kernels below share this per-fault loop; they differ in where the faults
+// come from and where a survivor's state goes.
 // ===================================================================================
-__global__ void __launch_bounds__(1024)
-heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
-    extern __shared__ __align__(16) uint32_t hsm[];
-    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
-    uint32_t *bm = hsm;                  // [nwn] dirty nodes
-    uint32_t *cnt = bm + nwn;            // [max_levels] dirty nodes per level
-    uint32_t *dbm = cnt + S.max_levels;  // [nwd] nets that differ this cycle
-    uint32_t *dlist = dbm + nwd;         // [HEAVY_DLIST] words of dbm to clear
-    // the range ring holds 8-byte entries: start it on an even word (heavy_smem_bytes agrees)
-    const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + 1) & ~(size_t)1;
-    uint2 *frange = reinterpret_cast<uint2 *>(hsm + fr_words);   // [HEAVY_FRANGE]
-    // one bit per level that has dirty nodes: the level loop visits only those
-    unsigned long long *lvm = reinterpret_cast<unsigned long long *>(frange + HEAVY_FRANGE);
-    const uint32_t nlw = (S.max_levels + 63) / 64;
-    __shared__ unsigned long long s_item;
-    __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
-    __shared__ unsigned long long s_load;
-    const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
-    const uint32_t lane = tid & 31u, warp = tid >> 5;
-    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
-    uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
-    uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
+constexpr uint32_t HEAVY_PREFETCH = 4;
 
-    for (uint32_t i = tid; i < nwn; i += B) bm[i] = 0;
-    for (uint32_t i = tid; i < S.max_levels; i += B) cnt[i] = 0;
-    for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
-    for (uint32_t i = tid; i < nlw; i += B) lvm[i] = 0;
-    if (tid == 0) s_nfr = 0;
-    __syncthreads();
+// Shared scalars of one heavy CTA.
+struct HeavyVars {
+    unsigned long long load;   // node evaluations of the current fault
+    uint32_t t;                // next active cycle, found by warp 0
+    uint32_t nreg_new;         // register diffs latched this cycle
+    uint32_t minport;          // lowest output port that differs this cycle
+    uint32_t site_seeded;      // a register diff already covered the fault site
+    uint32_t nd;               // words of the net bitmap to clear
+    uint32_t nfr;              // fan-out ranges appended this cycle
+    uint32_t nl;               // dirty nodes gathered for the current level
+};
+
+// Views of the heavy kernels' dynamic shared memory (heavy_smem_bytes sizes the same layout).
+struct HeavySmem {
+    uint32_t *bm;                 // [nwn] dirty nodes
+    uint32_t *cnt;                // [max_levels] dirty nodes per level
+    uint32_t *dbm;                // [nwd] nets that differ this cycle
+    uint32_t *dlist;              // [HEAVY_DLIST] words of dbm to clear
+    uint32_t *nlist;              // [HEAVY_NLIST] dirty nodes of the current level
+    uint2 *frange;                // [HEAVY_FRANGE] fan-out ranges (8-byte aligned)
+    unsigned long long *lvm;      // [nlw] one bit per level that has dirty nodes
+    uint32_t nwd, nlw;
+};
+
+__device__ __forceinline__ HeavySmem heavy_layout(uint32_t *hsm, const HeavyScratch &S) {
+    HeavySmem m;
+    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
+    m.nwd = nwd;
+    m.nlw = (S.max_levels + 63) / 64;
+    m.bm = hsm;
+    m.cnt = m.bm + nwn;
+    m.dbm = m.cnt + S.max_levels;
+    m.dlist = m.dbm + nwd;
+    m.nlist = m.dlist + HEAVY_DLIST;
+    const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + HEAVY_NLIST + 1) & ~(size_t)1;
+    m.frange = reinterpret_cast<uint2 *>(hsm + fr_words);
+    m.lvm = reinterpret_cast<unsigned long long *>(m.frange + HEAVY_FRANGE);
+    return m;
+}
+
+// Zero the bitmaps and counters once per CTA; every fault leaves them zero again.
+__device__ __forceinline__ void heavy_zero(const HeavySmem &m, const HeavyScratch &S, HeavyVars &V) {
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
+    for (uint32_t i = tid; i < nwn; i += B) m.bm[i] = 0;
+    for (uint32_t i = tid; i < S.max_levels; i += B) m.cnt[i] = 0;
+    for (uint32_t i = tid; i < nwd; i += B) m.dbm[i] = 0;
+    for (uint32_t i = tid; i < m.nlw; i += B) m.lvm[i] = 0;
+    if (tid == 0) { V.nfr = 0; V.nl = 0; V.load = 0; }
+}
+
+// Loads issued where they stand: volatile, so the compiler does not sink them into the
+// branch that consumes them and they travel together with the operand loads.
+__device__ __forceinline__ uint32_t ld_early_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_early_u16(const uint16_t *p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
+// Outcome of one heavy fault's run.
+struct HeavyRun {
+    uint32_t t;        // in: first cycle; out: first cycle not completed (see status)
+    uint32_t nreg;     // in: register diffs in half 0; out: in half `cur`
+    uint32_t cur;      // out: the half of regR/regV that holds the live register diffs
+    int status;        // 0 alive at tend, 1 detected at t, 3 over the load budget
+    int32_t det_cycle, det_port;
+};
+
+// Simulate fault fid from cycle r.t until it is detected, exceeds the load budget or
+// reaches tend. Cycles with no register diff and an inactive site are skipped without
+// work. V.load accumulates the node evaluations; the caller zeroes it per fault. Every
+// thread of the CTA calls this together and leaves the shared bitmaps zero.
+__device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFaults &f, uint32_t fid,
+                                                uint32_t tend, unsigned long long budget,
+                                                const HeavySmem &sm, HeavyVars &V, uint64_t *fval,
+                                                uint32_t *regR, uint64_t *regV, uint32_t max_reg,
+                                                HeavyRun &r) {
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    const uint32_t I = D.I, IR = D.I + D.R, T = D.T, NL = D.n_levels;
+    const uint64_t *__restrict__ gcol = D.gcol;
+    const uint4 *__restrict__ netinfo = D.netinfo;
+    const uint32_t *__restrict__ fo_idx = D.fo_idx;
+    const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
+    const uint32_t *__restrict__ dreg_off = D.dreg_off;
+    const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
+    const uint32_t site = f.site[fid];
+    const uint32_t bit = f.bit[fid];
+    const bool sv = f.val[fid] != 0;
+    const uint64_t bmask = 1ull << bit;
+    const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
+    uint32_t *const bm = sm.bm, *const cnt = sm.cnt, *const dbm = sm.dbm;
+    unsigned long long *const lvm = sm.lvm;
+    const uint32_t nlw = sm.nlw;
+    uint32_t t = r.t, nreg = r.nreg, cur = 0;
+    int status = 0;
+    int32_t det_cycle = -1, det_port = -1;
+
+    // Consumer node c (at level lv) becomes dirty.
+    auto mark = [&](uint32_t c, uint32_t lv) {
+        const uint32_t b1 = 1u << (c & 31u);
+        const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
+        if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
+    };
+    // The consumers of fan-out entries [e0, e1) with a stride: all threads share a long
+    // range in expand(); one thread marks a short one.
+    auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
+        for (uint32_t e = e0 + first; e < e1; e += step) mark(__ldg(fo_idx + e), __ldg(fo_lvl + e));
+    };
+    // Ranges live in a ring indexed by a per-cycle append counter V.nfr; fr_begin (the
+    // same in every thread, advanced only after a barrier) is the first unexpanded one.
+    uint32_t fr_begin = 0;
+    auto expand = [&]() {   // call after a barrier
+        const uint32_t end = V.nfr;
+        const uint32_t n = min(end - fr_begin, HEAVY_FRANGE);
+        for (uint32_t k = 0; k < n; ++k) {
+            const uint2 fr = sm.frange[(fr_begin + k) % HEAVY_FRANGE];
+            mark_range(fr.x, fr.y, tid, B);
+        }
+        fr_begin = end;
+    };
+    // A net that differs this cycle: its value, its flag, a detecting port, and the
+    // registers it drives whose latched value differs too (into half nb).
+    auto keep_value = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni, uint32_t nb) {
+        fval[net] = v;
+        const uint32_t wbit = 1u << (net & 31u);
+        if (!atomicOr(&dbm[net >> 5], wbit)) {   // first bit of this word: remember the word
+            const uint32_t k = atomicAdd(&V.nd, 1u);
+            if (k < HEAVY_DLIST) sm.dlist[k] = net >> 5;
+        }
+        const uint32_t p = ni_port(ni.w);
+        if (p != NI_NO_PORT) atomicMin(&V.minport, p);
+        uint32_t nr = ni_nreg(ni.w);
+        if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
+        for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
+            const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+            const uint64_t wm = wmask(rec >> 25);
+            const uint64_t qv = v & wm;
+            if (qv != (g & wm)) {
+                const uint32_t k = atomicAdd(&V.nreg_new, 1u);
+                regR[nb * max_reg + k] = rec & 0x1FFFFFFu;
+                regV[nb * max_reg + k] = qv;
+            }
+        }
+    };
+    // Its consumers: a long list goes to the ring (marked here if the ring is full).
+    auto keep_fanout = [&](uint4 ni) {
+        if (ni.y - ni.x > HEAVY_INLINE_FANOUT) {
+            const uint32_t k = atomicAdd(&V.nfr, 1u);
+            if (k - fr_begin < HEAVY_FRANGE) sm.frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
+            else mark_range(ni.x, ni.y, 0, 1);
+        } else {
+            mark_range(ni.x, ni.y, 0, 1);
+        }
+    };
+    auto lookup = [&](uint32_t x) -> uint64_t {
+        if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
+        return __ldg(gcol + (size_t)x * T + t);
+    };
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(q.heavy_head, 1ull);
-        __syncthreads();
-        const unsigned long long idx = s_item;
-        const uint32_t n_items = min(*((volatile uint32_t *)q.heavy_count), q.heavy_cap);
-        if (idx >= n_items) break;
-        const HeavyItem &it = q.heavy_items[idx];
-        const uint32_t fid = it.fault;
-        const DevDesign &D = designs[f.design[fid]];
-        const uint32_t I = D.I, IR = D.I + D.R, T = D.T, NL = D.n_levels;
-        const uint64_t *__restrict__ gcol = D.gcol;
-        const uint4 *__restrict__ netinfo = D.netinfo;
-        const uint32_t *__restrict__ fo_idx = D.fo_idx;
-        const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
-        const uint32_t *__restrict__ dreg_off = D.dreg_off;
-        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
-        const uint32_t site = f.site[fid];
-        const uint32_t bit = f.bit[fid];
-        const bool sv = f.val[fid] != 0;
-        const uint64_t bmask = 1ull << bit;
-        const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
-        uint32_t t = it.t, nreg = it.nreg, cur = 0;
-        const uint32_t t_start = it.t;
-        for (uint32_t k = tid; k < nreg; k += B) {
-            regR[k] = it.reg_r[k];
-            regV[k] = it.reg_v[k];
+        if (nreg == 0) {   // nothing latched: jump to the next cycle the site is active
+            if (warp == 0 && f.act) {
+                if (lane == 0) V.t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
+            } else if (warp == 0) {
+                uint32_t found = tend;
+                for (uint32_t tt = t; tt < tend; tt += 32) {
+                    const uint32_t u = tt + lane;
+                    bool act = false;
+                    if (u < tend) act = ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)sv;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, act);
+                    if (bal) { found = tt + __ffs(bal) - 1; break; }
+                }
+                if (lane == 0) V.t = found;
+            }
+            __syncthreads();
+            t = V.t;
+            if (t >= tend) break;
         }
-        if (tid == 0) s_load = 0;
-        int status = 0;
-        int32_t det_cycle = -1, det_port = -1;
+        const uint32_t nb = cur ^ 1u;
+        if (tid == 0) { V.nreg_new = 0; V.minport = NI_NO_PORT; V.site_seeded = 0; V.nd = 0; V.nfr = 0; }
+        fr_begin = 0;
         __syncthreads();
 
-        // Mark the consumers of one fan-out range (all threads of the CTA share the work
-        // when called from expand(); a single thread when the range list is full).
-        auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
-            for (uint32_t e = e0 + first; e < e1; e += step) {
-                const uint32_t c = __ldg(fo_idx + e);
-                const uint32_t lv = __ldg(fo_lvl + e);
-                const uint32_t b1 = 1u << (c & 31u);
-                const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
-                if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
-            }
-        };
-        // Ranges live in a ring indexed by a per-cycle append counter s_nfr; fr_begin (the
-        // same in every thread, advanced only after a barrier) is the first unexpanded one.
-        uint32_t fr_begin = 0;
-        // Phase 2: every thread takes a share of every recorded range. Call after a barrier.
-        auto expand = [&]() {
-            const uint32_t end = s_nfr;
-            const uint32_t n = min(end - fr_begin, HEAVY_FRANGE);
-            for (uint32_t r = 0; r < n; ++r) {
-                const uint2 fr = frange[(fr_begin + r) % HEAVY_FRANGE];
-                mark_range(fr.x, fr.y, tid, B);
-            }
-            fr_begin = end;
-        };
-
-        for (;;) {
-            if (nreg == 0) {
-                if (warp == 0 && f.act) {
-                    if (lane == 0) s_t = next_active(f.act + (size_t)fid * f.act_stride, t, T);
-                } else if (warp == 0) {
-                    uint32_t found = T;
-                    for (uint32_t tt = t; tt < T; tt += 32) {
-                        const uint32_t u = tt + lane;
-                        bool act = false;
-                        if (u < T) act = ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)sv;
-                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, act);
-                        if (bal) { found = tt + __ffs(bal) - 1; break; }
-                    }
-                    if (lane == 0) s_t = found;
-                }
-                __syncthreads();
-                t = s_t;
-                if (t >= T) break;
-            }
-            const uint32_t nb = cur ^ 1u;
-            if (tid == 0) { s_nreg_new = 0; s_minport = NI_NO_PORT; s_site_seeded = 0; s_nd = 0; s_nfr = 0; }
-            fr_begin = 0;
-            __syncthreads();
-
-            // Keep a differing net: value, detection, latch, and its fan-out range.
-            auto keep = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
-                fval[net] = v;
-                const uint32_t wbit = 1u << (net & 31u);
-                const uint32_t old = atomicOr(&dbm[net >> 5], wbit);
-                if (!old) {   // first bit of this word: remember the word for clearing
-                    const uint32_t k = atomicAdd(&s_nd, 1u);
-                    if (k < HEAVY_DLIST) dlist[k] = net >> 5;
-                }
-                const uint32_t p = ni_port(ni.w);
-                if (p != NI_NO_PORT) atomicMin(&s_minport, p);
-                if (ni.y - ni.x > HEAVY_INLINE_FANOUT) {   // long list: all threads share it
-                    const uint32_t k = atomicAdd(&s_nfr, 1u);
-                    if (k - fr_begin < HEAVY_FRANGE) frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
-                    else mark_range(ni.x, ni.y, 0, 1);   // ring full: mark here
-                } else if (ni.y > ni.x) {
-                    mark_range(ni.x, ni.y, 0, 1);
-                }
-                uint32_t nr = ni_nreg(ni.w);
-                if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
-                for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                    const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
-                    const uint32_t r = rec & 0x1FFFFFFu;
-                    const uint64_t wm = wmask(rec >> 25);
-                    const uint64_t qv = v & wm;
-                    if (qv != (g & wm)) {
-                        const uint32_t k = atomicAdd(&s_nreg_new, 1u);
-                        regR[nb * S.max_reg + k] = r;
-                        regV[nb * S.max_reg + k] = qv;
-                    }
-                }
-            };
-            auto lookup = [&](uint32_t x) -> uint64_t {
-                if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
-                return __ldg(gcol + (size_t)x * T + t);
-            };
-
-            for (uint32_t k = tid; k < nreg; k += B) {
-                const uint32_t net = I + regR[cur * S.max_reg + k];
-                uint64_t qv = regV[cur * S.max_reg + k];
-                const uint4 ni = __ldg(netinfo + net);
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (net == site) { qv = force_bit(qv, bmask, sv); s_site_seeded = 1; }
-                if (qv != g) keep(net, qv, g, ni);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                if (site < IR && !s_site_seeded) {
-                    const uint64_t g = __ldg(scol + t);
-                    const uint64_t fv = force_bit(g, bmask, sv);
-                    if (fv != g) keep(site, fv, g, __ldg(netinfo + site));
-                }
-                if (site >= IR) {
-                    const uint32_t c = site - IR;
-                    const uint32_t b1 = 1u << (c & 31u);
-                    const uint32_t old = atomicOr(&bm[c >> 5], b1);
-                    const uint32_t lv = __ldg(D.node_level + c);
-                    if (!(old & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
-                }
-            }
-            __syncthreads();
-            expand();
-            __syncthreads();
-            uint32_t my_load = 0;
-            for (uint32_t L = 0;;) {
-                // next level with dirty nodes (bits are only ever set above the current level)
-                uint32_t lw = L >> 6;
-                unsigned long long m = lw < nlw ? lvm[lw] & (~0ull << (L & 63u)) : 0ull;
-                while (!m && ++lw < nlw) m = lvm[lw];
-                if (!m) break;
-                L = (lw << 6) + (uint32_t)(__ffsll((long long)m) - 1);
-                if (L >= NL) break;
-                const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
-                const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
-                for (uint32_t w = w0 + tid; w <= w1; w += B) {
-                    uint32_t m = 0xFFFFFFFFu;
-                    if (w == w0) m &= 0xFFFFFFFFu << (lo & 31u);
-                    if (w == w1 && (hi & 31u)) m &= (1u << (hi & 31u)) - 1u;
-                    if (!(bm[w] & m)) continue;
-                    uint32_t bits = atomicAnd(&bm[w], ~m) & m;
-                    while (bits) {
-                        const uint32_t j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint32_t n = (w << 5) + j;
-                        const uint32_t net = IR + n;
-                        // independent loads first: descriptor, net record, good value
-                        const uint4 d = __ldg(D.desc + n);
-                        const uint4 ni = __ldg(netinfo + net);
-                        const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                        const uint32_t op = meta_op(d.w);
-                        const int no = n_operands(op);
-                        uint64_t a = 0, b = 0, c = 0;
-                        if (no >= 1) a = lookup(d.x);
-                        if (no >= 2) b = lookup(d.y);
-                        if (no >= 3) c = lookup(d.z);
-                        uint64_t v = eval_op(d, a, b, c);
-                        if (net == site) v = force_bit(v, bmask, sv);
-                        ++my_load;
-                        if (v != g) keep(net, v, g, ni);
-                    }
-                }
-                __syncthreads();
-                if (s_nfr != fr_begin) {   // uniform: read after the barrier
-                    expand();
-                    __syncthreads();
-                }
-                if (tid == 0) {
-                    cnt[L] = 0;
-                    atomicAnd(&lvm[L >> 6], ~(1ull << (L & 63u)));
-                }
-                __syncthreads();
-                ++L;
-            }
-            if (my_load) atomicAdd(&s_load, (unsigned long long)my_load);
-            __syncthreads();
-            // clear the net bitmap for the next cycle
-            const uint32_t nd = s_nd;
-            if (nd <= HEAVY_DLIST) {
-                for (uint32_t k = tid; k < nd; k += B) dbm[dlist[k]] = 0;
-            } else {
-                for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
-            }
-            if (s_minport != NI_NO_PORT) {
-                det_cycle = (int32_t)t;
-                det_port = (int32_t)s_minport;
-                status = 1;
-                break;
-            }
-            nreg = s_nreg_new;
-            cur = nb;
-            if (++t >= T) break;
-            if (q.fault_budget && (f.load[fid] + s_load) > q.fault_budget) { status = 3; break; }
-            __syncthreads();
+        // registers that carry a difference into this cycle
+        for (uint32_t k = tid; k < nreg; k += B) {
+            const uint32_t net = I + regR[cur * max_reg + k];
+            uint64_t qv = regV[cur * max_reg + k];
+            const uint4 ni = __ldg(netinfo + net);
+            const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+            if (net == site) { qv = force_bit(qv, bmask, sv); V.site_seeded = 1; }
+            if (qv != g) { keep_value(net, qv, g, ni, nb); keep_fanout(ni); }
         }
         __syncthreads();
         if (tid == 0) {
-            f.load[fid] += s_load;
-            f.res_det[fid] = status == 1 ? 1 : status == 3 ? 255 : 0;
-            f.res_cycle[fid] = det_cycle;
-            f.res_port[fid] = det_port;
-            if (status == 3) atomicAdd(q.budget_hit, 1ull);
-            atomicAdd(q.counters + 0, (unsigned long long)s_load);
-            const uint32_t t_end = status == 1 ? t + 1 : min(t, T);
+            if (site < IR && !V.site_seeded) {   // input or register site
+                const uint64_t g = __ldg(scol + t);
+                const uint64_t fv = force_bit(g, bmask, sv);
+                if (fv != g) {
+                    const uint4 ni = __ldg(netinfo + site);
+                    keep_value(site, fv, g, ni, nb);
+                    keep_fanout(ni);
+                }
+            }
+            if (site >= IR) mark(site - IR, __ldg(D.node_level + site - IR));   // node site
+        }
+        __syncthreads();
+        expand();
+        __syncthreads();
+
+        uint32_t my_load = 0;
+        // Evaluate dirty node n; keep its value if it differs from the good machine.
+        auto eval_node = [&](uint32_t n) {
+            const uint32_t net = IR + n;
+            const uint4 d = __ldg(D.desc + n);
+            const uint4 ni = __ldg(netinfo + net);
+            const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+            const uint32_t nf = ni.y - ni.x;
+            uint32_t pc[HEAVY_PREFETCH], pl[HEAVY_PREFETCH];
+#pragma unroll
+            for (uint32_t k = 0; k < HEAVY_PREFETCH; ++k) {
+                pc[k] = 0;
+                pl[k] = 0;
+                if (nf <= HEAVY_PREFETCH && k < nf) {
+                    pc[k] = ld_early_u32(fo_idx + ni.x + k);
+                    pl[k] = ld_early_u16(fo_lvl + ni.x + k);
+                }
+            }
+            const uint32_t op = meta_op(d.w);
+            const int no = n_operands(op);
+            uint64_t a = 0, b = 0, c = 0;
+            if (no >= 1) a = lookup(d.x);
+            if (no >= 2) b = lookup(d.y);
+            if (no >= 3) c = lookup(d.z);
+            uint64_t v = eval_op(d, a, b, c);
+            if (net == site) v = force_bit(v, bmask, sv);
+            ++my_load;
+            if (v != g) {
+                keep_value(net, v, g, ni, nb);
+                if (nf <= HEAVY_PREFETCH) {
+#pragma unroll
+                    for (uint32_t k = 0; k < HEAVY_PREFETCH; ++k)
+                        if (k < nf) mark(pc[k], pl[k]);
+                } else {
+                    keep_fanout(ni);
+                }
+            }
+        };
+
+        for (uint32_t L = 0;;) {
+            // next level with dirty nodes (bits are only ever set above the current level)
+            uint32_t lw = L >> 6;
+            unsigned long long m = lw < nlw ? lvm[lw] & (~0ull << (L & 63u)) : 0ull;
+            while (!m && ++lw < nlw) m = lvm[lw];
+            if (!m) break;
+            L = (lw << 6) + (uint32_t)(__ffsll((long long)m) - 1);
+            if (L >= NL) break;
+            const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
+            const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
+            // every mark into level L was made at a lower level, behind a barrier: the
+            // count is exact and the same in all threads
+            const bool gather = cnt[L] <= HEAVY_NLIST;
+            for (uint32_t w = w0 + tid; w <= w1; w += B) {
+                uint32_t wm = 0xFFFFFFFFu;
+                if (w == w0) wm &= 0xFFFFFFFFu << (lo & 31u);
+                if (w == w1 && (hi & 31u)) wm &= (1u << (hi & 31u)) - 1u;
+                if (!(bm[w] & wm)) continue;
+                uint32_t bits = atomicAnd(&bm[w], ~wm) & wm;
+                if (gather) {
+                    uint32_t k = atomicAdd(&V.nl, (uint32_t)__popc(bits));
+                    for (; bits; bits &= bits - 1, ++k)
+                        if (k < HEAVY_NLIST) sm.nlist[k] = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+                } else {
+                    for (; bits; bits &= bits - 1) eval_node((w << 5) + (uint32_t)(__ffs(bits) - 1));
+                }
+            }
+            if (gather) {
+                __syncthreads();
+                const uint32_t nl = min(V.nl, HEAVY_NLIST);
+                for (uint32_t i = tid; i < nl; i += B) eval_node(sm.nlist[i]);
+            }
+            __syncthreads();
+            if (V.nfr != fr_begin) {   // uniform: read after the barrier
+                expand();
+                __syncthreads();
+            }
+            if (tid == 0) {
+                cnt[L] = 0;
+                atomicAnd(&lvm[L >> 6], ~(1ull << (L & 63u)));
+                V.nl = 0;
+            }
+            __syncthreads();
+            ++L;
+        }
+        if (my_load) atomicAdd(&V.load, (unsigned long long)my_load);
+        __syncthreads();
+        // clear the net bitmap for the next cycle
+        const uint32_t nd = V.nd;
+        if (nd <= HEAVY_DLIST) {
+            for (uint32_t k = tid; k < nd; k += B) dbm[sm.dlist[k]] = 0;
+        } else {
+            for (uint32_t i = tid; i < sm.nwd; i += B) dbm[i] = 0;
+        }
+        if (V.minport != NI_NO_PORT) {
+            det_cycle = (int32_t)t;
+            det_port = (int32_t)V.minport;
+            status = 1;
+            break;
+        }
+        nreg = V.nreg_new;
+        cur = nb;
+        if (++t >= tend) break;
+        if (budget && (f.load[fid] + V.load) > budget) { status = 3; break; }
+        __syncthreads();
+    }
+    r.t = t;
+    r.nreg = nreg;
+    r.cur = cur;
+    r.status = status;
+    r.det_cycle = det_cycle;
+    r.det_port = det_port;
+}
+
+__global__ void __launch_bounds__(1024)
+heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    __shared__ HeavyVars V;
+    __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_n_items;
+    const HeavySmem sm = heavy_layout(hsm, S);
+    const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
+    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
+    uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
+    uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
+    heavy_zero(sm, S, V);
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(q.heavy_head, 1ull);
+            s_n_items = min(*((volatile uint32_t *)q.heavy_count), q.heavy_cap);
+        }
+        __syncthreads();
+        const unsigned long long idx = s_item;
+        if (idx >= s_n_items) break;
+        const HeavyItem &it = q.heavy_items[idx];
+        const uint32_t fid = it.fault;
+        const DevDesign &D = designs[f.design[fid]];
+        for (uint32_t k = tid; k < it.nreg; k += B) {
+            regR[k] = it.reg_r[k];
+            regV[k] = it.reg_v[k];
+        }
+        if (tid == 0) V.load = 0;
+        __syncthreads();
+        HeavyRun r{it.t, it.nreg, 0, 0, -1, -1};
+        heavy_run_fault(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        __syncthreads();
+        if (tid == 0) {
+            f.load[fid] += V.load;
+            f.res_det[fid] = r.status == 1 ? 1 : r.status == 3 ? 255 : 0;
+            f.res_cycle[fid] = r.det_cycle;
+            f.res_port[fid] = r.det_port;
+            if (r.status == 3) atomicAdd(q.budget_hit, 1ull);
+            atomicAdd(q.counters + 0, V.load);
+            const uint32_t t_end = r.status == 1 ? r.t + 1 : min(r.t, D.T);
+            atomicAdd(q.counters + 1, (unsigned long long)(t_end - it.t));
+        }
+        __syncthreads();
+    }
+}
+
+// Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
+// from the last window and those promoted in this one; survivors carry their register
+// diffs to the next window through the pool.
+__global__ void __launch_bounds__(1024)
+heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    __shared__ HeavyVars V;
+    __shared__ unsigned long long s_item, s_off;
+    const HeavySmem sm = heavy_layout(hsm, S);
+    const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
+    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
+    uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
+    uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
+    heavy_zero(sm, S, V);
+    __syncthreads();
+
+    // written before this launch by earlier work on the stream: the same in every thread
+    const uint32_t n_carry = *q.n_carry_in, pb = *q.prom_begin, pe = *q.prom_end;
+    const unsigned long long n_items = (unsigned long long)n_carry + (pe - pb);
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(q.head, 1ull);
+        __syncthreads();
+        const unsigned long long idx = s_item;
+        if (idx >= n_items) break;
+        const bool carried = idx < n_carry;
+        // carried faults back to front: the slowest of the last window first
+        const HeavyCarry cin = carried ? q.carry_in[n_carry - 1 - (uint32_t)idx] : HeavyCarry{0, 0, 0};
+        const HeavyItem &it = q.prom[pb + (carried ? 0 : idx - n_carry)];
+        const uint32_t fid = carried ? cin.fault : it.fault;
+        const DevDesign &D = designs[f.design[fid]];
+        const uint32_t tend = min(q.t1, D.T);   // this window ends at tend
+        const uint32_t t_start = carried ? q.t0 : it.t;
+        const uint32_t nreg0 = carried ? cin.nreg : it.nreg;
+        for (uint32_t k = tid; k < nreg0; k += B) {
+            regR[k] = carried ? q.pool_r_in[cin.off + k] : it.reg_r[k];
+            regV[k] = carried ? q.pool_v_in[cin.off + k] : it.reg_v[k];
+        }
+        if (tid == 0) V.load = 0;
+        __syncthreads();
+        HeavyRun r{t_start, nreg0, 0, 0, -1, -1};
+        heavy_run_fault(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        __syncthreads();
+        const bool carry = r.status == 0 && tend < D.T;   // alive at the end of the window
+        if (carry) {
+            if (tid == 0) {
+                const unsigned long long off = atomicAdd(q.pool_top_out, (unsigned long long)r.nreg);
+                s_off = off + r.nreg <= q.pool_cap ? off : ~0ull;
+                if (s_off == ~0ull) atomicOr(q.err, 2u);
+            }
+            __syncthreads();
+            const unsigned long long off = s_off;
+            if (off != ~0ull) {
+                for (uint32_t k = tid; k < r.nreg; k += B) {
+                    q.pool_r_out[off + k] = regR[r.cur * S.max_reg + k];
+                    q.pool_v_out[off + k] = regV[r.cur * S.max_reg + k];
+                }
+                if (tid == 0) q.carry_out[atomicAdd(q.n_carry_out, 1u)] = HeavyCarry{fid, r.nreg, off};
+            }
+        }
+        if (tid == 0) {
+            f.load[fid] += V.load;
+            if (!carry) {
+                f.res_det[fid] = r.status == 1 ? 1 : r.status == 3 ? 255 : 0;
+                f.res_cycle[fid] = r.det_cycle;
+                f.res_port[fid] = r.det_port;
+            }
+            if (r.status == 3) atomicAdd(q.budget_hit, 1ull);
+            atomicAdd(q.counters + 0, V.load);
+            const uint32_t t_end = r.status == 1 ? r.t + 1 : min(r.t, tend);
             atomicAdd(q.counters + 1, (unsigned long long)(t_end - t_start));
         }
         __syncthreads();
@@ -1041,293 +1238,6 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
 #undef HP
 }
 
-// Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
-// from the last window and those promoted in this one; survivors carry their register
-// diffs to the next window through the pool.
-__global__ void __launch_bounds__(1024)
-heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
-    extern __shared__ __align__(16) uint32_t hsm[];
-    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
-    uint32_t *bm = hsm;                  // [nwn] dirty nodes
-    uint32_t *cnt = bm + nwn;            // [max_levels] dirty nodes per level
-    uint32_t *dbm = cnt + S.max_levels;  // [nwd] nets that differ this cycle
-    uint32_t *dlist = dbm + nwd;         // [HEAVY_DLIST] words of dbm to clear
-    // the range ring holds 8-byte entries: start it on an even word (heavy_smem_bytes agrees)
-    const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + 1) & ~(size_t)1;
-    uint2 *frange = reinterpret_cast<uint2 *>(hsm + fr_words);   // [HEAVY_FRANGE]
-    // one bit per level that has dirty nodes: the level loop visits only those
-    unsigned long long *lvm = reinterpret_cast<unsigned long long *>(frange + HEAVY_FRANGE);
-    const uint32_t nlw = (S.max_levels + 63) / 64;
-    __shared__ unsigned long long s_item, s_off;
-    __shared__ uint32_t s_t, s_nreg_new, s_minport, s_site_seeded, s_nd, s_nfr;
-    __shared__ unsigned long long s_load;
-    const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
-    const uint32_t lane = tid & 31u, warp = tid >> 5;
-    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
-    uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
-    uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
-
-    for (uint32_t i = tid; i < nwn; i += B) bm[i] = 0;
-    for (uint32_t i = tid; i < S.max_levels; i += B) cnt[i] = 0;
-    for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
-    for (uint32_t i = tid; i < nlw; i += B) lvm[i] = 0;
-    if (tid == 0) s_nfr = 0;
-    __syncthreads();
-
-    const uint32_t n_carry = *q.n_carry_in, pb = *q.prom_begin, pe = *q.prom_end;
-    const unsigned long long n_items = (unsigned long long)n_carry + (pe - pb);
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(q.head, 1ull);
-        __syncthreads();
-        const unsigned long long idx = s_item;
-        if (idx >= n_items) break;
-        const bool carried = idx < n_carry;
-        // carried faults back to front: the slowest of the last window first
-        const HeavyCarry cin = carried ? q.carry_in[n_carry - 1 - (uint32_t)idx] : HeavyCarry{0, 0, 0};
-        const HeavyItem &it = q.prom[pb + (carried ? 0 : idx - n_carry)];
-        const uint32_t fid = carried ? cin.fault : it.fault;
-        const DevDesign &D = designs[f.design[fid]];
-        const uint32_t I = D.I, IR = D.I + D.R, T = D.T, NL = D.n_levels;
-        const uint32_t tend = min(q.t1, T);     // this window ends at tend
-        const uint64_t *__restrict__ gcol = D.gcol;
-        const uint4 *__restrict__ netinfo = D.netinfo;
-        const uint32_t *__restrict__ fo_idx = D.fo_idx;
-        const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
-        const uint32_t *__restrict__ dreg_off = D.dreg_off;
-        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
-        const uint32_t site = f.site[fid];
-        const uint32_t bit = f.bit[fid];
-        const bool sv = f.val[fid] != 0;
-        const uint64_t bmask = 1ull << bit;
-        const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
-        uint32_t t = carried ? q.t0 : it.t, nreg = carried ? cin.nreg : it.nreg, cur = 0;
-        const uint32_t t_start = t;
-        for (uint32_t k = tid; k < nreg; k += B) {
-            regR[k] = carried ? q.pool_r_in[cin.off + k] : it.reg_r[k];
-            regV[k] = carried ? q.pool_v_in[cin.off + k] : it.reg_v[k];
-        }
-        if (tid == 0) s_load = 0;
-        int status = 0;
-        int32_t det_cycle = -1, det_port = -1;
-        __syncthreads();
-
-        // Mark the consumers of one fan-out range (all threads of the CTA share the work
-        // when called from expand(); a single thread when the range list is full).
-        auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
-            for (uint32_t e = e0 + first; e < e1; e += step) {
-                const uint32_t c = __ldg(fo_idx + e);
-                const uint32_t lv = __ldg(fo_lvl + e);
-                const uint32_t b1 = 1u << (c & 31u);
-                const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
-                if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
-            }
-        };
-        // Ranges live in a ring indexed by a per-cycle append counter s_nfr; fr_begin (the
-        // same in every thread, advanced only after a barrier) is the first unexpanded one.
-        uint32_t fr_begin = 0;
-        // Phase 2: every thread takes a share of every recorded range. Call after a barrier.
-        auto expand = [&]() {
-            const uint32_t end = s_nfr;
-            const uint32_t n = min(end - fr_begin, HEAVY_FRANGE);
-            for (uint32_t r = 0; r < n; ++r) {
-                const uint2 fr = frange[(fr_begin + r) % HEAVY_FRANGE];
-                mark_range(fr.x, fr.y, tid, B);
-            }
-            fr_begin = end;
-        };
-
-        for (;;) {
-            if (nreg == 0) {
-                if (warp == 0 && f.act) {
-                    if (lane == 0) s_t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
-                } else if (warp == 0) {
-                    uint32_t found = tend;
-                    for (uint32_t tt = t; tt < tend; tt += 32) {
-                        const uint32_t u = tt + lane;
-                        bool act = false;
-                        if (u < tend) act = ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)sv;
-                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, act);
-                        if (bal) { found = tt + __ffs(bal) - 1; break; }
-                    }
-                    if (lane == 0) s_t = found;
-                }
-                __syncthreads();
-                t = s_t;
-                if (t >= tend) break;
-            }
-            const uint32_t nb = cur ^ 1u;
-            if (tid == 0) { s_nreg_new = 0; s_minport = NI_NO_PORT; s_site_seeded = 0; s_nd = 0; s_nfr = 0; }
-            fr_begin = 0;
-            __syncthreads();
-
-            // Keep a differing net: value, detection, latch, and its fan-out range.
-            auto keep = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
-                fval[net] = v;
-                const uint32_t wbit = 1u << (net & 31u);
-                const uint32_t old = atomicOr(&dbm[net >> 5], wbit);
-                if (!old) {   // first bit of this word: remember the word for clearing
-                    const uint32_t k = atomicAdd(&s_nd, 1u);
-                    if (k < HEAVY_DLIST) dlist[k] = net >> 5;
-                }
-                const uint32_t p = ni_port(ni.w);
-                if (p != NI_NO_PORT) atomicMin(&s_minport, p);
-                if (ni.y - ni.x > HEAVY_INLINE_FANOUT) {   // long list: all threads share it
-                    const uint32_t k = atomicAdd(&s_nfr, 1u);
-                    if (k - fr_begin < HEAVY_FRANGE) frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
-                    else mark_range(ni.x, ni.y, 0, 1);   // ring full: mark here
-                } else if (ni.y > ni.x) {
-                    mark_range(ni.x, ni.y, 0, 1);
-                }
-                uint32_t nr = ni_nreg(ni.w);
-                if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
-                for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                    const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
-                    const uint32_t r = rec & 0x1FFFFFFu;
-                    const uint64_t wm = wmask(rec >> 25);
-                    const uint64_t qv = v & wm;
-                    if (qv != (g & wm)) {
-                        const uint32_t k = atomicAdd(&s_nreg_new, 1u);
-                        regR[nb * S.max_reg + k] = r;
-                        regV[nb * S.max_reg + k] = qv;
-                    }
-                }
-            };
-            auto lookup = [&](uint32_t x) -> uint64_t {
-                if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
-                return __ldg(gcol + (size_t)x * T + t);
-            };
-
-            for (uint32_t k = tid; k < nreg; k += B) {
-                const uint32_t net = I + regR[cur * S.max_reg + k];
-                uint64_t qv = regV[cur * S.max_reg + k];
-                const uint4 ni = __ldg(netinfo + net);
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (net == site) { qv = force_bit(qv, bmask, sv); s_site_seeded = 1; }
-                if (qv != g) keep(net, qv, g, ni);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                if (site < IR && !s_site_seeded) {
-                    const uint64_t g = __ldg(scol + t);
-                    const uint64_t fv = force_bit(g, bmask, sv);
-                    if (fv != g) keep(site, fv, g, __ldg(netinfo + site));
-                }
-                if (site >= IR) {
-                    const uint32_t c = site - IR;
-                    const uint32_t b1 = 1u << (c & 31u);
-                    const uint32_t old = atomicOr(&bm[c >> 5], b1);
-                    const uint32_t lv = __ldg(D.node_level + c);
-                    if (!(old & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
-                }
-            }
-            __syncthreads();
-            expand();
-            __syncthreads();
-            uint32_t my_load = 0;
-            for (uint32_t L = 0;;) {
-                // next level with dirty nodes (bits are only ever set above the current level)
-                uint32_t lw = L >> 6;
-                unsigned long long m = lw < nlw ? lvm[lw] & (~0ull << (L & 63u)) : 0ull;
-                while (!m && ++lw < nlw) m = lvm[lw];
-                if (!m) break;
-                L = (lw << 6) + (uint32_t)(__ffsll((long long)m) - 1);
-                if (L >= NL) break;
-                const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
-                const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
-                for (uint32_t w = w0 + tid; w <= w1; w += B) {
-                    uint32_t m = 0xFFFFFFFFu;
-                    if (w == w0) m &= 0xFFFFFFFFu << (lo & 31u);
-                    if (w == w1 && (hi & 31u)) m &= (1u << (hi & 31u)) - 1u;
-                    if (!(bm[w] & m)) continue;
-                    uint32_t bits = atomicAnd(&bm[w], ~m) & m;
-                    while (bits) {
-                        const uint32_t j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint32_t n = (w << 5) + j;
-                        const uint32_t net = IR + n;
-                        // independent loads first: descriptor, net record, good value
-                        const uint4 d = __ldg(D.desc + n);
-                        const uint4 ni = __ldg(netinfo + net);
-                        const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                        const uint32_t op = meta_op(d.w);
-                        const int no = n_operands(op);
-                        uint64_t a = 0, b = 0, c = 0;
-                        if (no >= 1) a = lookup(d.x);
-                        if (no >= 2) b = lookup(d.y);
-                        if (no >= 3) c = lookup(d.z);
-                        uint64_t v = eval_op(d, a, b, c);
-                        if (net == site) v = force_bit(v, bmask, sv);
-                        ++my_load;
-                        if (v != g) keep(net, v, g, ni);
-                    }
-                }
-                __syncthreads();
-                if (s_nfr != fr_begin) {   // uniform: read after the barrier
-                    expand();
-                    __syncthreads();
-                }
-                if (tid == 0) {
-                    cnt[L] = 0;
-                    atomicAnd(&lvm[L >> 6], ~(1ull << (L & 63u)));
-                }
-                __syncthreads();
-                ++L;
-            }
-            if (my_load) atomicAdd(&s_load, (unsigned long long)my_load);
-            __syncthreads();
-            // clear the net bitmap for the next cycle
-            const uint32_t nd = s_nd;
-            if (nd <= HEAVY_DLIST) {
-                for (uint32_t k = tid; k < nd; k += B) dbm[dlist[k]] = 0;
-            } else {
-                for (uint32_t i = tid; i < nwd; i += B) dbm[i] = 0;
-            }
-            if (s_minport != NI_NO_PORT) {
-                det_cycle = (int32_t)t;
-                det_port = (int32_t)s_minport;
-                status = 1;
-                break;
-            }
-            nreg = s_nreg_new;
-            cur = nb;
-            if (++t >= tend) break;
-            if (q.fault_budget && (f.load[fid] + s_load) > q.fault_budget) { status = 3; break; }
-            __syncthreads();
-        }
-        __syncthreads();
-        const bool carry = status == 0 && tend < T;   // alive at the end of the window
-        if (carry) {
-            if (tid == 0) {
-                const unsigned long long off = atomicAdd(q.pool_top_out, (unsigned long long)nreg);
-                s_off = off + nreg <= q.pool_cap ? off : ~0ull;
-                if (s_off == ~0ull) atomicOr(q.err, 2u);
-            }
-            __syncthreads();
-            const unsigned long long off = s_off;
-            if (off != ~0ull) {
-                for (uint32_t k = tid; k < nreg; k += B) {
-                    q.pool_r_out[off + k] = regR[cur * S.max_reg + k];
-                    q.pool_v_out[off + k] = regV[cur * S.max_reg + k];
-                }
-                if (tid == 0) q.carry_out[atomicAdd(q.n_carry_out, 1u)] = HeavyCarry{fid, nreg, off};
-            }
-        }
-        if (tid == 0) {
-            f.load[fid] += s_load;
-            if (!carry) {
-                f.res_det[fid] = status == 1 ? 1 : status == 3 ? 255 : 0;
-                f.res_cycle[fid] = det_cycle;
-                f.res_port[fid] = det_port;
-            }
-            if (status == 3) atomicAdd(q.budget_hit, 1ull);
-            atomicAdd(q.counters + 0, (unsigned long long)s_load);
-            const uint32_t t_end = status == 1 ? t + 1 : min(t, tend);
-            atomicAdd(q.counters + 1, (unsigned long long)(t_end - t_start));
-        }
-        __syncthreads();
-    }
-}
-
 // ===================================================================================
 // Plain GPU form: one thread per fault, one flat launch per design (and wave), no
 // queue, no heavy path. Same sparse-diff method with unbounded per-thread state in
@@ -1562,7 +1472,7 @@ cudaError_t launch_light_window(const DevDesign *d_designs, DevFaults f, WinLigh
 }
 
 size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net) {
-    size_t words = (size_t)(max_node + 31) / 32 + max_levels + (max_net + 31) / 32 + HEAVY_DLIST;
+    size_t words = (size_t)(max_node + 31) / 32 + max_levels + (max_net + 31) / 32 + HEAVY_DLIST + HEAVY_NLIST;
     words = (words + 1) & ~(size_t)1;   // 8-byte alignment of the range list
     return words * sizeof(uint32_t) + HEAVY_FRANGE * sizeof(uint2) +
            (size_t)((max_levels + 63) / 64) * sizeof(unsigned long long);
