@@ -121,7 +121,13 @@ typedef struct {
                                 window of cycles, the good trace of the next window, the light
                                 kernel and the heavy kernel overlap on three streams; 0 = each
                                 fault runs its whole timeline in one light/heavy pass */
-    uint32_t reserved[6];
+    int32_t  good_cluster;   /* good-trace form: 0 = auto (one CTA with the net values in
+                                shared memory when the design fits, else the smallest
+                                thread-block cluster whose CTAs hold them in distributed
+                                shared memory, else one CTA over the global trace);
+                                1 = one CTA; 2, 4, 8 or 16 = clusters of that many CTAs
+                                (RTLFS_E_ARG when a design cannot run that way) */
+    uint32_t reserved[5];
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */

@@ -12,6 +12,7 @@
 
 #include <cuda_bf16.h>
 #include <deque>
+#include <memory>
 
 #include <algorithm>
 #include <cmath>
@@ -85,12 +86,23 @@ struct Design {
     // good trace
     DBuf<uint64_t> d_rows, d_gcol;
     bool trace_valid = false;
+    // cluster good-trace plans, indexed by log2 of the cluster size (built on first use)
+    struct ClusterPlan {
+        uint32_t own = 0, rown = 0, max_ch = 0;
+        size_t smem = 0;
+        int usable = -1;   // clusters of this size can be resident (-1: not asked yet)
+        DBuf<uint4> d_desc, d_chunk, d_reg;
+        DBuf<uint32_t> d_ch_off, d_reg_off;
+    };
+    std::unique_ptr<ClusterPlan> plan[5];
 };
 
 }  // namespace
 
 struct GoodLaunch {
     uint32_t n_smem = 0, n_glob = 0, max_net_s = 0, max_reg_s = 0, max_ch_s = 0, max_ch_g = 0;
+    uint32_t n_cl[5] = {};        // designs on each cluster list (index log2 of the cluster size)
+    size_t smem_cl[5] = {};       // shared memory per CTA of each cluster launch
 };
 
 struct rtlfs_ctx {
@@ -119,7 +131,8 @@ struct rtlfs_ctx {
     std::vector<cudaEvent_t> ev_win;   // [4][nw]: light start/end, heavy start/end
     cudaEvent_t ev[8] = {};
     DBuf<DevDesign> d_designs;
-    DBuf<uint32_t> d_list_smem, d_list_glob;
+    DBuf<uint32_t> d_list_smem, d_list_glob, d_list_cl[5];
+    uint32_t good_cluster = 0;         // good-trace mode of the next run (rtlfs_run_opts)
     bool faults_dirty = true;
     uint32_t F = 0;
     std::vector<uint32_t> f_first;    // first global fault id of each design
@@ -456,52 +469,204 @@ DevDesign dev_view(const Design &D) {
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;   // dynamic shared memory of one good-trace CTA
 
-// Allocate traces and upload the design table and good-trace launch lists.
+// Cluster plan of a design for clusters of C CTAs: every level's nodes split into C
+// contiguous shares (CTA k owns its shares in level order, one value word per node),
+// registers split into C contiguous index blocks (their home CTAs), every operand
+// rewritten as the location of its value, and each CTA's chunk list (at least one chunk
+// per level, so every CTA joins every level's barrier).
+int build_cluster_plan(rtlfs_ctx *ctx, Design &D, uint32_t C, int lc) {
+    auto P = std::make_unique<Design::ClusterPlan>();
+    const uint32_t I = D.I, R = D.R, N = D.N, IR = I + R, NL = D.n_levels;
+    std::vector<uint32_t> own(C, 0), node_rank(N), node_slot(N);
+    std::vector<std::vector<uint4>> chunks(C);
+    for (uint32_t l = 0; l < NL; ++l) {
+        const uint32_t lo = D.lvl_start[l], n = D.lvl_start[l + 1] - lo;
+        for (uint32_t k = 0; k < C; ++k) {
+            const uint32_t a = lo + (uint32_t)((uint64_t)n * k / C);
+            const uint32_t b = lo + (uint32_t)((uint64_t)n * (k + 1) / C);
+            for (uint32_t x = a; x < b; ++x) { node_rank[x] = k; node_slot[x] = own[k] + (x - a); }
+            if (a == b) chunks[k].push_back(make_uint4(own[k], 0x80000000u, a, 0));
+            for (uint32_t x = a; x < b; x += GOOD_BLOCK) {
+                const uint32_t m = std::min(GOOD_BLOCK, b - x);
+                chunks[k].push_back(make_uint4(own[k] + (x - a), m | (x + m == b ? 0x80000000u : 0u), x, 0));
+            }
+            own[k] += b - a;
+        }
+    }
+    std::vector<uint32_t> reg_off(C + 1), reg_home(R);
+    for (uint32_t k = 0; k <= C; ++k) reg_off[k] = (uint32_t)((uint64_t)R * k / C);
+    for (uint32_t k = 0; k < C; ++k)
+        for (uint32_t r = reg_off[k]; r < reg_off[k + 1]; ++r) reg_home[r] = k;
+    P->own = *std::max_element(own.begin(), own.end());
+    P->rown = 0;
+    for (uint32_t k = 0; k < C; ++k) P->rown = std::max(P->rown, reg_off[k + 1] - reg_off[k]);
+    if ((uint64_t)P->own + 2ull * P->rown + I > CL_WORD) return fail(ctx, RTLFS_E_ARG, "design too large for a cluster plan");
+    auto loc = [&](uint32_t net) -> uint32_t {
+        if (net < I) return CL_SELF | (P->own + 2 * P->rown + net);
+        if (net < IR) {
+            const uint32_t r = net - I, k = reg_home[r];
+            return CL_REG | (k << CL_RANK_SHIFT) | (P->own + r - reg_off[k]);
+        }
+        const uint32_t x = net - IR;
+        return (node_rank[x] << CL_RANK_SHIFT) | node_slot[x];
+    };
+    std::vector<uint4> cdesc((size_t)C * P->own, make_uint4(0, 0, 0, 0));
+    for (uint32_t x = 0; x < N; ++x) {
+        uint4 d = D.desc[x];
+        const int no = n_ops(meta_op(d.w));
+        if (no >= 1) d.x = loc(d.x);
+        if (no >= 2) d.y = loc(d.y);
+        if (no >= 3) d.z = loc(d.z);
+        cdesc[(size_t)node_rank[x] * P->own + node_slot[x]] = d;
+    }
+    std::vector<uint4> creg(R);
+    for (uint32_t r = 0; r < R; ++r) creg[r] = make_uint4(r, loc(D.reg_d[r]), D.net_w[I + r], D.reg_d[r]);
+    std::vector<uint4> call;
+    std::vector<uint32_t> ch_off(C + 1, 0);
+    P->max_ch = 0;
+    for (uint32_t k = 0; k < C; ++k) {
+        ch_off[k] = (uint32_t)call.size();
+        call.insert(call.end(), chunks[k].begin(), chunks[k].end());
+        P->max_ch = std::max<uint32_t>(P->max_ch, (uint32_t)chunks[k].size());
+    }
+    ch_off[C] = (uint32_t)call.size();
+    P->smem = good_cluster_smem_bytes(P->own, P->rown, I, P->max_ch);
+    CU(P->d_desc.upload(cdesc));
+    CU(P->d_chunk.upload(call));
+    CU(P->d_reg.upload(creg));
+    CU(P->d_ch_off.upload(ch_off));
+    CU(P->d_reg_off.upload(reg_off));
+    D.plan[lc] = std::move(P);
+    return RTLFS_OK;
+}
+
+// Whether clusters of C CTAs can run design D's good trace; builds the plan on first use.
+int cluster_usable(rtlfs_ctx *ctx, Design &D, uint32_t C, int lc, bool *ok) {
+    *ok = false;
+    if (!D.plan[lc]) {
+        int rc = build_cluster_plan(ctx, D, C, lc);
+        if (rc != RTLFS_OK) return rc;
+    }
+    Design::ClusterPlan &P = *D.plan[lc];
+    if (P.smem > SMEM_LIMIT) return RTLFS_OK;
+    if ((uint64_t)D.T * P.max_ch >= (1ull << 32)) return RTLFS_OK;
+    if (P.usable < 0) P.usable = good_cluster_max_active(C, P.smem) > 0 ? 1 : 0;
+    *ok = P.usable == 1;
+    return RTLFS_OK;
+}
+
+// Allocate traces, choose each design's good-trace form and upload the design table and
+// the launch lists: one CTA with net values in shared memory when the design fits, else
+// the smallest cluster whose CTAs hold the design in distributed shared memory, else one
+// CTA with net values in the global trace. ctx->good_cluster overrides the choice:
+// 1 = one CTA, 2..16 = clusters of that size.
 int prepare_good(rtlfs_ctx *ctx) {
     std::vector<DevDesign> tab;
-    std::vector<uint32_t> l_smem, l_glob;
-    uint32_t max_net_s = 0, max_reg_s = 0, max_ch_s = 0, max_ch_g = 0;
+    std::vector<uint32_t> l_smem, l_glob, l_cl[5];
+    GoodLaunch g{};
+    const uint32_t force = ctx->good_cluster;
     for (size_t i = 0; i < ctx->designs.size(); ++i) {
         Design &D = *ctx->designs[i];
         const size_t cells = (size_t)D.n_net * D.T;
         CU(D.d_rows.reserve(cells));
         CU(D.d_gcol.reserve(cells));
-        tab.push_back(dev_view(D));
+        DevDesign v = dev_view(D);
         const uint32_t nch = (uint32_t)D.chunks.size();
-        // net values in shared memory when the design fits together with the designs
-        // already on the shared-memory list (one launch covers the whole list)
-        const uint32_t mn = std::max(max_net_s, D.n_net), mr = std::max(max_reg_s, D.R);
-        const uint32_t mc = std::max(max_ch_s, nch);
-        if (good_smem_bytes(true, mn, mr, mc) <= SMEM_LIMIT) {
-            l_smem.push_back((uint32_t)i);
-            max_net_s = mn; max_reg_s = mr; max_ch_s = mc;
+        int lc = 0;   // log2 of the chosen cluster size; 0 = one CTA
+        if (force >= 2) {
+            lc = 1;
+            while ((1u << lc) < force) ++lc;
+            bool ok = false;
+            int rc = cluster_usable(ctx, D, 1u << lc, lc, &ok);
+            if (rc != RTLFS_OK) return rc;
+            if (!ok) return fail(ctx, RTLFS_E_ARG, "design %zu cannot run its good trace on clusters of %u", i, 1u << lc);
         } else {
-            l_glob.push_back((uint32_t)i);
-            max_ch_g = std::max(max_ch_g, nch);
+            // net values in shared memory when the design fits together with the designs
+            // already on the shared-memory list (one launch covers the whole list)
+            const uint32_t mn = std::max(g.max_net_s, D.n_net), mr = std::max(g.max_reg_s, D.R);
+            const uint32_t mc = std::max(g.max_ch_s, nch);
+            if (good_smem_bytes(true, mn, mr, mc) <= SMEM_LIMIT) {
+                l_smem.push_back((uint32_t)i);
+                g.max_net_s = mn; g.max_reg_s = mr; g.max_ch_s = mc;
+            } else {
+                if (force == 0) {
+                    for (lc = 1; (1u << lc) <= CL_MAX; ++lc) {
+                        bool ok = false;
+                        int rc = cluster_usable(ctx, D, 1u << lc, lc, &ok);
+                        if (rc != RTLFS_OK) return rc;
+                        if (ok) break;
+                    }
+                    if ((1u << lc) > CL_MAX) lc = 0;
+                }
+                if (lc == 0) {
+                    l_glob.push_back((uint32_t)i);
+                    g.max_ch_g = std::max(g.max_ch_g, nch);
+                }
+            }
         }
+        if (lc > 0) {
+            const Design::ClusterPlan &P = *D.plan[lc];
+            v.cl_own = P.own; v.cl_rown = P.rown;
+            v.cl_desc = P.d_desc.p; v.cl_chunk = P.d_chunk.p; v.cl_ch_off = P.d_ch_off.p;
+            v.cl_reg = P.d_reg.p; v.cl_reg_off = P.d_reg_off.p;
+            l_cl[lc].push_back((uint32_t)i);
+            g.smem_cl[lc] = std::max(g.smem_cl[lc], P.smem);
+        }
+        tab.push_back(v);
     }
     CU(ctx->d_designs.upload(tab));
     CU(ctx->d_list_smem.upload(l_smem));
     CU(ctx->d_list_glob.upload(l_glob));
-    if (good_smem_bytes(false, 0, 0, max_ch_g) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
-    for (Design *D : ctx->designs)   // chunk instances of one good-trace launch fit 32 bits
+    for (int lc = 1; lc < 5; ++lc) {
+        CU(ctx->d_list_cl[lc].upload(l_cl[lc]));
+        g.n_cl[lc] = (uint32_t)l_cl[lc].size();
+    }
+    if (good_smem_bytes(false, 0, 0, g.max_ch_g) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
+    for (uint32_t i : l_smem) {   // chunk instances of one good-trace launch fit 32 bits
+        const Design *D = ctx->designs[i];
         if ((uint64_t)D->T * D->chunks.size() >= (1ull << 32))
             return fail(ctx, RTLFS_E_ARG, "cycles x chunks too large for one launch: use windows");
+    }
+    for (uint32_t i : l_glob) {
+        const Design *D = ctx->designs[i];
+        if ((uint64_t)D->T * D->chunks.size() >= (1ull << 32))
+            return fail(ctx, RTLFS_E_ARG, "cycles x chunks too large for one launch: use windows");
+    }
     CU(ctx->d_err.reserve(1));
-    ctx->gl = {(uint32_t)l_smem.size(), (uint32_t)l_glob.size(), max_net_s, max_reg_s, max_ch_s, max_ch_g};
+    g.n_smem = (uint32_t)l_smem.size();
+    g.n_glob = (uint32_t)l_glob.size();
+    ctx->gl = g;
+    return RTLFS_OK;
+}
+
+// Good-trace launches of cycles [t0, t1) for every list on `stream`; *n counts them.
+int launch_good_lists(rtlfs_ctx *ctx, cudaStream_t stream, uint32_t t0, uint32_t t1, uint32_t *n) {
+    const GoodLaunch &g = ctx->gl;
+    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
+                         g.max_ch_s, true, ctx->d_err.p, stream, t0, t1));
+    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
+                         ctx->d_err.p, stream, t0, t1));
+    *n += (g.n_smem ? 1 : 0) + (g.n_glob ? 1 : 0);
+    for (int lc = 1; lc < 5; ++lc) {
+        if (!g.n_cl[lc]) continue;
+        CU(launch_good_cluster(ctx->d_designs.p, ctx->d_list_cl[lc].p, g.n_cl[lc], 1u << lc, g.smem_cl[lc],
+                               ctx->d_err.p, stream, t0, t1));
+        ++*n;
+    }
     return RTLFS_OK;
 }
 
 // Enqueue good trace + transposes on s_main (stream work only; prepare_good first).
-int launch_good(rtlfs_ctx *ctx) {
-    const GoodLaunch &g = ctx->gl;
+int launch_good(rtlfs_ctx *ctx, uint32_t *n_launches = nullptr) {
+    uint32_t n = 0;
     CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
-    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
-                         g.max_ch_s, true, ctx->d_err.p, ctx->s_main));
-    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
-                         ctx->d_err.p, ctx->s_main));
-    for (Design *D : ctx->designs)
+    int rc = launch_good_lists(ctx, ctx->s_main, 0, 0xFFFFFFFFu, &n);
+    if (rc != RTLFS_OK) return rc;
+    for (Design *D : ctx->designs) {
         CU(launch_transpose(D->d_gcol.p, D->d_rows.p, D->n_net, D->T, ctx->s_main));
+        ++n;
+    }
+    if (n_launches) *n_launches += n;
     return RTLFS_OK;
 }
 
@@ -643,7 +808,11 @@ int rtlfs_create(rtlfs_ctx **out, int device) {
         CU(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device));
         CU(cudaStreamCreateWithFlags(&ctx->s_main, cudaStreamNonBlocking));
         CU(cudaStreamCreateWithFlags(&ctx->s_heavy, cudaStreamNonBlocking));
-        CU(cudaStreamCreateWithFlags(&ctx->s_good, cudaStreamNonBlocking));
+        // the good trace of the next window gates every fault of that window: its CTAs
+        // take free SMs before pending light or heavy CTAs
+        int lo_prio = 0, hi_prio = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+        CU(cudaStreamCreateWithPriority(&ctx->s_good, cudaStreamNonBlocking, hi_prio));
         CU(cudaEventCreateWithFlags(&ctx->ev_wg, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&ctx->ev_wl, cudaEventDisableTiming));
         for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
@@ -773,6 +942,9 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     const int hblock = o.heavy_block > 0 ? o.heavy_block : 32;
     if (lblock < 32 || lblock > 256 || (lblock & 31)) return fail(ctx, RTLFS_E_ARG, "light_block must be a multiple of 32 in 32..256");
     if (hblock < 32 || hblock > 1024 || (hblock & 31)) return fail(ctx, RTLFS_E_ARG, "heavy_block must be a multiple of 32 in 32..1024");
+    if (o.good_cluster < 0 || o.good_cluster > (int)CL_MAX || (o.good_cluster > 1 && (o.good_cluster & (o.good_cluster - 1))))
+        return fail(ctx, RTLFS_E_ARG, "good_cluster must be 0, 1, 2, 4, 8 or 16");
+    ctx->good_cluster = (uint32_t)o.good_cluster;
     CU(cudaSetDevice(ctx->device));
     const auto t_host0 = std::chrono::steady_clock::now();
     int rc = build_faults(ctx);
@@ -897,18 +1069,15 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(cudaEventRecord(ctx->ev_wl, ctx->s_main));
         CU(cudaStreamWaitEvent(ctx->s_good, ctx->ev_wl, 0));
         CU(cudaStreamWaitEvent(ctx->s_heavy, ctx->ev_wl, 0));
-        const GoodLaunch &g = ctx->gl;
         const uint32_t lblocks = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(((int64_t)F + lblock - 1) / lblock,
                                                                                   (int64_t)lgrid_cap));
         for (uint32_t w = 0; w < nw; ++w) {
             const uint32_t t0 = w * W, t1 = std::min(t0 + W, Tmax);
             // good trace of the window
-            CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
-                                 g.max_ch_s, true, ctx->d_err.p, ctx->s_good, t0, t1));
-            CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
-                                 ctx->d_err.p, ctx->s_good, t0, t1));
+            int r3 = launch_good_lists(ctx, ctx->s_good, t0, t1, &launches);
+            if (r3 != RTLFS_OK) return r3;
             CU(launch_transpose_window(ctx->d_designs.p, (uint32_t)ctx->designs.size(), max_net, t0, t1, ctx->s_good));
-            launches += 3;
+            ++launches;
             if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, t0, t1, ctx->s_good)); ++launches; }
             if (w == 0) CU(cudaEventRecord(ev[1], ctx->s_good));
             CU(cudaEventRecord(ctx->ev_wg, ctx->s_good));
@@ -1009,9 +1178,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
         CU(cudaMemcpyAsync(ctx->d_counters.p, cinit, 4 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
         if (F) CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
-        int r2 = launch_good(ctx);
+        int r2 = launch_good(ctx, &launches);
         if (r2 != RTLFS_OK) return r2;
-        launches += 2 + (uint32_t)ctx->designs.size();
         if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, 0, Tmax, ctx->s_main)); ++launches; }
         CU(cudaEventRecord(ev[1], ctx->s_main));
         if (dev_sched) {
@@ -1069,6 +1237,9 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
                                ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv});
+        for (int lc = 1; lc < 5; ++lc)
+            key.insert(key.end(), {(uint64_t)g.n_cl[lc], (uint64_t)g.smem_cl[lc],
+                                   (uint64_t)(uintptr_t)ctx->d_list_cl[lc].p});
         for (Design *D : ctx->designs)
             key.insert(key.end(), {(uint64_t)(uintptr_t)D->d_rows.p, (uint64_t)(uintptr_t)D->d_gcol.p,
                                    D->n_net, D->T});

@@ -60,7 +60,26 @@ struct DevDesign {
     const uint64_t *stim;       // [T][I]
     uint64_t *rows;             // [T][n_net] good trace, one row per cycle
     uint64_t *gcol;             // [n_net][T] good trace, one column per net
+    // Cluster good trace (designs too large for one CTA's shared memory): the layout of
+    // one CTA's value area and each CTA's descriptor, chunk and register lists.
+    uint32_t cl_own;            // node values per CTA (words)
+    uint32_t cl_rown;           // registers per CTA (words per bank)
+    const uint4    *cl_desc;    // [C][cl_own] descriptors, operands as cluster locations
+    const uint4    *cl_chunk;   // chunk lists {first slot, count | 1<<31 at a level's end, first node, 0}
+    const uint32_t *cl_ch_off;  // [C + 1] chunk list of each CTA
+    const uint4    *cl_reg;     // {register, D location, width, D net} by home CTA
+    const uint32_t *cl_reg_off; // [C + 1] registers of each CTA (a contiguous index range)
 };
+
+// A net's location for the cluster good trace, 32 bits: the word in the holding CTA's
+// value area (node values [0, own), register banks [own, own + 2 rown), inputs after
+// them), the holder's rank in the cluster, and two flags: a register (add the bank of
+// the cycle's parity) and an input (every CTA holds a copy: read the local one).
+constexpr uint32_t CL_WORD = 0x00FFFFFFu;
+constexpr uint32_t CL_RANK_SHIFT = 24;
+constexpr uint32_t CL_REG = 1u << 28;
+constexpr uint32_t CL_SELF = 1u << 29;
+constexpr uint32_t CL_MAX = 16;   // largest cluster (non-portable size on sm_103a)
 
 // All faults of all designs, concatenated in design order.
 struct DevFaults {
@@ -201,6 +220,14 @@ cudaError_t launch_heavy_window(const DevDesign *d_designs, DevFaults f, WinHeav
                                 HeavyScratch s, int block, int grid, cudaStream_t stream);
 cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,
                              cudaStream_t stream);
+// Shared memory of one cluster good-trace CTA for a design's layout.
+size_t good_cluster_smem_bytes(uint32_t own, uint32_t rown, uint32_t n_inputs, uint32_t max_chunks);
+// Clusters of C CTAs with `smem` bytes each that can be resident at once (0: none).
+int good_cluster_max_active(uint32_t C, size_t smem);
+// Good trace of the listed designs over cycles [t_begin, t_end), one cluster of C CTAs each.
+cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *design_list,
+                                uint32_t n_list, uint32_t C, size_t smem, uint32_t *err,
+                                cudaStream_t stream, uint32_t t_begin, uint32_t t_end);
 cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int cap, int block,
                          int grid, cudaStream_t stream);
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,

@@ -202,6 +202,157 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
     }
 }
 
+// ===================================================================================
+// Good-machine trace of a design too large for one CTA's shared memory: one cluster of
+// C CTAs (2..16) per design. Each CTA owns a contiguous share of every level's nodes and
+// keeps their values of the current cycle in its own shared memory; a node reads each
+// operand where it lives through distributed shared memory (mapa + ld.shared::cluster),
+// its descriptor carrying the operand's location (CL_*). A register lives in its home
+// CTA in two banks selected by the cycle's parity: the latch of cycle t fills bank
+// (t+1)&1 while other registers' latches may still read Q_t from bank t&1 (a register
+// fed by a register). Every CTA keeps its own copy of the inputs. A cluster barrier
+// (release/acquire, so a level's values are visible cluster-wide) ends every level and
+// the latch. Each CTA streams its own descriptor list through shared memory by TMA as in
+// the single-CTA kernel; a level in which a CTA owns no node is an empty chunk that only
+// advances the buffer ring and joins the barrier.
+// ===================================================================================
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_ctas() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 64-bit load from the same shared-memory offset in CTA `rank` of this cluster.
+__device__ __forceinline__ uint64_t dsm_load(uint32_t local_addr, uint32_t rank) {
+    uint32_t ra;
+    uint64_t v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local_addr), "r"(rank));
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra));
+    return v;
+}
+
+__global__ void __launch_bounds__(GOOD_BLOCK, 1)
+good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
+                    uint32_t *err, uint32_t t_begin, uint32_t t_end) {
+    extern __shared__ __align__(128) uint64_t gsm[];
+    const uint32_t rank = cluster_rank(), C = cluster_ctas();
+    const DevDesign &D = designs[list[blockIdx.x / C]];
+    const uint32_t I = D.I, IR = I + D.R, n_net = D.n_net;
+    const uint32_t T = min(D.T, t_end);
+    if (t_begin >= T) return;   // the same in every CTA of the cluster
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t own = D.cl_own, rown = D.cl_rown;
+    const size_t vwords = (size_t)own + 2 * (size_t)rown + I;
+    uint64_t *qv = gsm + own;            // [2][rown] register banks (node values [own] before)
+    uint64_t *inv = qv + 2 * rown;       // [I] inputs
+    uint4 *stage = reinterpret_cast<uint4 *>(gsm + ((vwords + 15) & ~(size_t)15));   // [NBUF][GOOD_BLOCK]
+    const uint32_t c0 = D.cl_ch_off[rank], NC = D.cl_ch_off[rank + 1] - c0;
+    uint4 *ch = stage + GOOD_NBUF * GOOD_BLOCK;                                 // [NC]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(ch + NC);                     // [NBUF]
+    const uint4 *__restrict__ cdesc = D.cl_desc + (size_t)rank * own;
+    const uint4 *__restrict__ creg = D.cl_reg + D.cl_reg_off[rank];
+    const uint32_t NR = D.cl_reg_off[rank + 1] - D.cl_reg_off[rank];
+    const uint32_t base = smem_u32(gsm);
+    for (uint32_t c = tid; c < NC; c += B) ch[c] = D.cl_chunk[c0 + c];
+    if (tid == 0) {
+        for (int b = 0; b < GOOD_NBUF; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // registers entering t_begin: the reset value, or the latch of the previous window
+    for (uint32_t j = tid; j < NR; j += B) {
+        const uint4 g = creg[j];
+        uint64_t q = 0ull;
+        if (t_begin > 0) q = D.rows[(size_t)(t_begin - 1) * n_net + g.w] & wmask(g.z);
+        qv[(t_begin & 1u) * rown + j] = q;
+    }
+    // all CTAs of the cluster are running and initialised before any remote read
+    cluster_sync();
+
+    const uint32_t total = (T - t_begin) * NC;   // chunk instances (the host bounds it)
+    uint32_t cf = 0;
+    auto issue = [&](uint32_t buf) {             // thread 0: next chunk instance into buf
+        const uint4 b = ch[cf];
+        const uint32_t n = b.y & 0x7FFFFFFFu;
+        if (n) tma_issue(mbar + buf, stage + buf * GOOD_BLOCK, cdesc + b.x, n * 16u);
+        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(mbar + buf)) : "memory");
+        cf = cf + 1 == NC ? 0 : cf + 1;
+    };
+    if (tid == 0)
+        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && k < total; ++k) issue(k);
+    uint32_t kc = 0, buf = 0, par = 0;
+    bool failed = false;
+    uint32_t f_kc = 0, f_buf = 0, f_par = 0;     // where a staging wait ran out
+
+    for (uint32_t t = t_begin; t < T; ++t) {
+        uint64_t *row = D.rows + (size_t)t * n_net;
+        const uint32_t bank_off = (t & 1u) * rown;
+        // inputs of cycle t into this CTA's copy; CTA 0 writes them to the trace
+        for (uint32_t i = tid; i < I; i += B) {
+            const uint64_t v = __ldg(D.stim + (size_t)t * I + i) & wmask(D.net_w[i]);
+            inv[i] = v;
+            if (rank == 0) row[i] = v;
+        }
+        // this CTA's registers (a contiguous index range): Q of cycle t to the trace
+        for (uint32_t j = tid; j < NR; j += B) row[I + creg[j].x] = qv[bank_off + j];
+        __syncthreads();
+        auto fetch = [&](uint32_t e) -> uint64_t {
+            const uint32_t w = (e & CL_WORD) + ((e & CL_REG) ? bank_off : 0u);
+            const uint32_t r = (e & CL_SELF) ? rank : ((e >> CL_RANK_SHIFT) & 15u);
+            return dsm_load(base + w * 8u, r);
+        };
+        for (uint32_t c = 0; c < NC; ++c, ++kc) {
+            const uint4 b = ch[c];
+            const uint32_t n = b.y & 0x7FFFFFFFu;
+            const bool mine = tid < n && !failed;
+            const bool staged = mine ? mbar_wait(mbar + buf, par) : true;
+            if (mine && staged) {
+                const uint4 d0 = stage[buf * GOOD_BLOCK + tid];
+                const uint32_t op = meta_op(d0.w);
+                const int no = n_operands(op);
+                uint64_t a = 0, bb = 0, cc = 0;
+                if (no >= 1) a = fetch(d0.x);
+                if (no >= 2) bb = fetch(d0.y);
+                if (no >= 3) cc = fetch(d0.z);
+                const uint64_t v = eval_op(d0, a, bb, cc);
+                gsm[b.x + tid] = v;
+                row[IR + b.z + tid] = v;
+            }
+            // every thread is done with this buffer (and every wait succeeded): refill it
+            if (!__syncthreads_and(staged) && !failed) { failed = true; f_kc = kc; f_buf = buf; f_par = par; }
+            if (tid == 0 && !failed && kc + GOOD_NBUF < total) issue(buf);
+            if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
+            if (b.y & 0x80000000u) cluster_sync();   // a level is complete cluster-wide
+        }
+        // latch: Q of cycle t+1 into the other bank
+        for (uint32_t j = tid; j < NR; j += B) {
+            const uint4 g = creg[j];
+            qv[(rown - bank_off) + j] = failed ? 0ull : (fetch(g.y) & wmask(g.z));
+        }
+        cluster_sync();
+    }
+    if (failed && tid == 0) {
+        // a staging wait ran out: report it and give the copies still in flight a bounded
+        // chance to land before the CTA exits
+        atomicOr(err, 1u);
+        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && f_kc + k < total; ++k) {
+            mbar_wait(mbar + f_buf, f_par);
+            if (++f_buf == (uint32_t)GOOD_NBUF) { f_buf = 0; f_par ^= 1u; }
+        }
+    }
+}
+
 // rows[T][n_net] -> gcol[n_net][T], 32x32 tiles through shared memory.
 __global__ void transpose_kernel(uint64_t *__restrict__ gcol, const uint64_t *__restrict__ rows,
                                  uint32_t n_net, uint32_t T) {
@@ -1394,6 +1545,61 @@ cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design
                                                                       max_chunks, err, t_begin, t_end);
     }
     return cudaGetLastError();
+}
+
+size_t good_cluster_smem_bytes(uint32_t own, uint32_t rown, uint32_t n_inputs, uint32_t max_chunks) {
+    const size_t vwords = (size_t)own + 2 * (size_t)rown + n_inputs;
+    return ((vwords + 15) & ~(size_t)15) * sizeof(uint64_t) + (size_t)GOOD_NBUF * GOOD_BLOCK * 16 +
+           (size_t)max_chunks * 16 + GOOD_NBUF * sizeof(uint64_t);
+}
+
+static cudaError_t good_cluster_attrs(uint32_t C, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(good_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(good_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+int good_cluster_max_active(uint32_t C, size_t smem) {
+    if (good_cluster_attrs(C, smem) != cudaSuccess) { cudaGetLastError(); return 0; }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(GOOD_BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)good_cluster_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *design_list,
+                                uint32_t n_list, uint32_t C, size_t smem, uint32_t *err,
+                                cudaStream_t stream, uint32_t t_begin, uint32_t t_end) {
+    if (n_list == 0) return cudaSuccess;
+    cudaError_t e = good_cluster_attrs(C, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(n_list * C);
+    cfg.blockDim = dim3(GOOD_BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, good_cluster_kernel, d_designs, design_list, err, t_begin, t_end);
 }
 
 cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,

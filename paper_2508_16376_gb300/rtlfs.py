@@ -39,7 +39,8 @@ class rtlfs_run_opts(ctypes.Structure):
                 ("heavy_block", ctypes.c_int32), ("heavy_ctas", ctypes.c_int32),
                 ("heavy_frac", ctypes.c_float), ("use_graph", ctypes.c_int32),
                 ("fault_budget", ctypes.c_uint64), ("light_cap", ctypes.c_int32),
-                ("window", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 6)]
+                ("window", ctypes.c_int32), ("good_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32 * 5)]
 
 
 class rtlfs_stats(ctypes.Structure):

@@ -66,12 +66,14 @@ def test_good_trace_matches_oracle(maker, T):
 
 
 def test_good_trace_global_memory_path():
-    """A design too large for shared-memory net values runs the global-memory variant."""
+    """A design too large for shared-memory net values, kept on one CTA (good_cluster=1),
+    runs the variant whose net values live in the global trace."""
     d = synth.gen_datapath_fsm(5, 30000, 600, 32, 32, [16], 0.5, 20, 64, "big")
     stim = synth.stimulus(d, 64, 5)
     g, trace = oracle.good_run(d, stim, with_trace=True)
     with Simulator(0) as sim:
         sim.add(d, stim, synth.sample_faults(d, 10, 1))
+        sim.run(good_cluster=1)
         assert np.array_equal(sim.good_trace(0), trace)
 
 
