@@ -81,13 +81,40 @@ typedef struct {
 /* One stuck-at fault (8 bytes): bit `bit` of net `net` forced to `stuck` (0 or 1) every
  * time the net's value is produced -- input read, register read, node evaluation
  * (unified fault injection at the producing node, Sec. IV-A). A register fault forces
- * the Q its readers see; the register still stores its D value. */
+ * the Q its readers see; the register still stores its D value.
+ * Port faults (Sec. IV-A, Table I: a port fault is injected into a virtual node inserted
+ * for the port): net ids n_net + o, o < n_outputs, denote output port o -- a virtual node
+ * between the port's net and the port, so the fault changes what port o observes and
+ * nothing else (the net's other readers see its true value). An input port is its own
+ * net (ids below n_inputs): a fault there reaches every reader of the input. */
 typedef struct {
     uint32_t net;
     uint8_t  bit;       /* < width(net) */
     uint8_t  stuck;     /* 0 = stuck-at-0, 1 = stuck-at-1 */
     uint16_t reserved;
 } rtlfs_fault;
+
+/* Fault kinds of rtlfs_fault_ex (the fault function of Sec. IV-A, chosen per fault;
+ * transient models, Sec. V-A). A flip inverts bit `bit` during cycle `cycle` only:
+ *   SEU -- single-event upset of a register: the stored value of a register net has the
+ *          bit flipped for cycle `cycle`; the latch at the end of that cycle overwrites it,
+ *          so in a cycle-based model it acts as a one-cycle flip of the Q its readers see;
+ *   SET -- single-event transient on a combinational net (an input, a node or an output
+ *          port): the net's value is flipped during cycle `cycle`.
+ * A flip always makes the site differ in its cycle; before it the machines are equal. */
+#define RTLFS_FAULT_SA0  0
+#define RTLFS_FAULT_SA1  1
+#define RTLFS_FAULT_SEU  2   /* net must be a register (n_inputs <= net < n_inputs + n_regs) */
+#define RTLFS_FAULT_SET  3   /* net must be an input, a node or an output port */
+
+typedef struct {
+    uint32_t net;       /* as in rtlfs_fault, port ids included */
+    uint8_t  bit;       /* < width(net) */
+    uint8_t  kind;      /* RTLFS_FAULT_* */
+    uint16_t reserved;
+    uint32_t cycle;     /* cycle of an SEU/SET (any value; >= n_cycles never acts) */
+    uint32_t reserved2;
+} rtlfs_fault_ex;
 
 /* Per-fault result (12 bytes). Outputs are compared after the combinational settle of
  * cycle `cycle` (0-based), before the latch; `port` is the lowest differing output
@@ -121,13 +148,17 @@ typedef struct {
                                 window of cycles, the good trace of the next window, the light
                                 kernel and the heavy kernel overlap on three streams; 0 = each
                                 fault runs its whole timeline in one light/heavy pass */
+    int32_t  no_drop;        /* 1 = keep simulating a detected fault to the last cycle (the
+                                paper's evaluation protocol, Sec. V-A): the result keeps the
+                                first detection and rtlfs_mismatch_counts gives each fault's
+                                number of cycles with a differing output */
     int32_t  good_cluster;   /* good-trace form: 0 = auto (one CTA with the net values in
                                 shared memory when the design fits, else the smallest
                                 thread-block cluster whose CTAs hold them in distributed
                                 shared memory, else one CTA over the global trace);
                                 1 = one CTA; 2, 4, 8 or 16 = clusters of that many CTAs
                                 (RTLFS_E_ARG when a design cannot run that way) */
-    uint32_t reserved[5];
+    uint32_t reserved[4];
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */
@@ -187,6 +218,13 @@ int rtlfs_set_stimulus(rtlfs_ctx *ctx, uint32_t design_id, const uint64_t *input
 int rtlfs_set_faults(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults,
                      uint32_t n_faults);
 
+/* Fault list of a design with per-fault kinds: stuck-at, SEU and SET faults (see
+ * rtlfs_fault_ex). Validation as rtlfs_set_faults, plus: an SEU site must be a register,
+ * an SET site must not be (its flip is an SEU). Replaces an earlier list. Errors:
+ * RTLFS_E_ARG, RTLFS_E_NOMEM. */
+int rtlfs_set_faults_ex(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault_ex *faults,
+                        uint32_t n_faults);
+
 /* Simulate every loaded design's fault list under its stimulus (the whole hot path: good
  * trace, load prediction and queue order, light and heavy faulty machines with output
  * compare, fault dropping and register latch). out_per_design[d] is a caller buffer of
@@ -205,6 +243,12 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out_per_design);
 
 /* Counters and timings of the last rtlfs_run / rtlfs_run_plain. */
 int rtlfs_get_stats(const rtlfs_ctx *ctx, rtlfs_stats *out);
+
+/* After an rtlfs_run with no_drop = 1: for each fault of the design (in list order), the
+ * number of cycles in which some output port differs from the good machine (n-detection
+ * count; 0 = undetected). out[n_faults], caller-owned. RTLFS_E_STATE when the last run
+ * dropped faults or the fault list changed since. */
+int rtlfs_mismatch_counts(rtlfs_ctx *ctx, uint32_t design_id, uint32_t *out);
 
 /* Test hooks: the good machine's outputs out[n_cycles][n_outputs], or every net's value
  * out[n_cycles][n_nets] in the caller's net numbering, as computed by the last run (or

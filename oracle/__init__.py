@@ -58,7 +58,12 @@ def _open(path: str):
                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]
-    for f in (lib.oracle_topo_order, lib.oracle_good_run, lib.oracle_fault_sim):
+    lib.oracle_fault_sim_ex.argtypes = [P, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]
+    for f in (lib.oracle_topo_order, lib.oracle_good_run, lib.oracle_fault_sim, lib.oracle_fault_sim_ex):
         f.restype = ctypes.c_int
     return lib
 
@@ -153,7 +158,11 @@ def good_outputs(design, stim: np.ndarray) -> np.ndarray:
 def fault_sim(design, stim: np.ndarray, faults, threads: int = 1,
               gout: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     """Serial single-fault simulation of every fault; returns (detected u8, cycle i32,
-    port i32) per fault. `threads` host threads each take a contiguous slice."""
+    port i32) per fault. `threads` host threads each take a contiguous slice. Faults with
+    a `cycle` array (kinds 2 = SEU, 3 = SET in `val`) or port sites (net ids n_net + o)
+    go through the general entry point."""
+    if getattr(faults, "cycle", None) is not None or (len(faults) and int(np.max(faults.net)) >= design.n_net):
+        return fault_sim_ex(design, stim, faults, threads, gout)[:3]
     lib = _load()
     p = _Pinned(design)
     stim = np.ascontiguousarray(stim, np.uint64)
@@ -173,26 +182,69 @@ def fault_sim(design, stim: np.ndarray, faults, threads: int = 1,
     port = np.zeros(max(F, 1), np.int32)
     if F == 0:
         return det[:0], cyc[:0], port[:0]
-    threads = max(1, min(int(threads), F))
-    bounds = np.linspace(0, F, threads + 1).astype(np.int64)
 
-    def run(k):
-        lo, hi = int(bounds[k]), int(bounds[k + 1])
-        if hi <= lo:
-            return 0
+    def run(lo, hi):
         return lib.oracle_fault_sim(ctypes.byref(p.c), T, s.ctypes.data, g.ctypes.data, hi - lo,
                                     fnet[lo:].ctypes.data, fbit[lo:].ctypes.data,
                                     fval[lo:].ctypes.data, det[lo:].ctypes.data,
                                     cyc[lo:].ctypes.data, port[lo:].ctypes.data)
 
-    if threads == 1:
-        rcs = [run(0)]
+    _in_slices(run, F, threads)
+    return det[:F], cyc[:F], port[:F]
+
+
+def fault_sim_ex(design, stim: np.ndarray, faults, threads: int = 1,
+                 gout: Optional[np.ndarray] = None, no_drop: bool = False):
+    """The general form: per-fault kinds in `val` (0 SA0, 1 SA1, 2 SEU, 3 SET with the
+    flip cycle in `faults.cycle`), port sites (net ids n_net + o), and the no-drop mode.
+    Returns (detected u8, cycle i32, port i32, mismatch cycles u32) per fault."""
+    lib = _load()
+    p = _Pinned(design)
+    stim = np.ascontiguousarray(stim, np.uint64)
+    T = int(stim.shape[0])
+    if gout is None:
+        gout = good_outputs(design, stim)
+    g = np.ascontiguousarray(gout, np.uint64)
+    if g.size == 0:
+        g = np.zeros(1, np.uint64)
+    s = stim if stim.size else np.zeros(1, np.uint64)
+    F = len(faults)
+    fnet = np.ascontiguousarray(faults.net, np.uint32)
+    fbit = np.ascontiguousarray(faults.bit, np.uint8)
+    fkind = np.ascontiguousarray(faults.val, np.uint8)
+    cycle = getattr(faults, "cycle", None)
+    fcyc = np.ascontiguousarray(cycle if cycle is not None else np.zeros(F), np.uint32)
+    det = np.zeros(max(F, 1), np.uint8)
+    cyc = np.zeros(max(F, 1), np.int32)
+    port = np.zeros(max(F, 1), np.int32)
+    mism = np.zeros(max(F, 1), np.uint32)
+    if F == 0:
+        return det[:0], cyc[:0], port[:0], mism[:0]
+
+    def run(lo, hi):
+        return lib.oracle_fault_sim_ex(ctypes.byref(p.c), T, s.ctypes.data, g.ctypes.data, hi - lo,
+                                       fnet[lo:].ctypes.data, fbit[lo:].ctypes.data,
+                                       fkind[lo:].ctypes.data, fcyc[lo:].ctypes.data,
+                                       1 if no_drop else 0, det[lo:].ctypes.data,
+                                       cyc[lo:].ctypes.data, port[lo:].ctypes.data,
+                                       mism[lo:].ctypes.data)
+
+    _in_slices(run, F, threads)
+    return det[:F], cyc[:F], port[:F], mism[:F]
+
+
+def _in_slices(run, F: int, threads: int) -> None:
+    """run(lo, hi) on `threads` contiguous slices of [0, F) in parallel host threads."""
+    threads = max(1, min(int(threads), F))
+    bounds = np.linspace(0, F, threads + 1).astype(np.int64)
+    spans = [(int(bounds[k]), int(bounds[k + 1])) for k in range(threads) if bounds[k + 1] > bounds[k]]
+    if len(spans) == 1:
+        rcs = [run(*spans[0])]
     else:
-        with ThreadPoolExecutor(threads) as ex:
-            rcs = list(ex.map(run, range(threads)))
+        with ThreadPoolExecutor(len(spans)) as ex:
+            rcs = list(ex.map(lambda sp: run(*sp), spans))
     if any(rc != 0 for rc in rcs):
         raise ValueError("combinational cycle")
-    return det[:F], cyc[:F], port[:F]
 
 
 def fault_cycles(detected: np.ndarray, cycle: np.ndarray, T: int) -> int:

@@ -26,6 +26,19 @@
  *                detects the fault: result (1, t, o) and the machine stops (fault
  *                dropping). After T cycles with no difference: (0, -1, -1).
  *
+ * Other fault models through the same fault function (Sec. IV-A: a virtual faultyVal;
+ * Sec. V-A: transient faults by overriding it):
+ *   kind 2 (SEU, on a register) and kind 3 (SET, on an input or node net) flip bit b of
+ *                the site in one cycle c only: a register's stored value flipped for cycle
+ *                c is what its readers see in that cycle, and the latch at the end of c
+ *                overwrites it, so both are "flip when t == c".
+ *   port faults: site ids n_net + o name output port o, a virtual node between the
+ *                port's net and the port (Sec. IV-A, Table I): the fault function applies
+ *                to what port o observes, and to nothing else.
+ *   no-drop mode (the paper's evaluation keeps every fault, Sec. V-A): the machine runs
+ *                all T cycles; the result keeps the first detection and counts the cycles
+ *                in which some port differs.
+ *
  * Readings where the paper is silent (it works on Verilog through iverilog):
  *   2-valued logic (no X/Z); registers reset to 0; outputs sampled after the settle of
  *   cycle t and before the latch (a register-driven output shows Q_t); cycle index
@@ -141,25 +154,32 @@ static uint64_t eval_node(const oracle_design *d, const uint64_t *net, int32_t i
 }
 
 /* One machine over T cycles. With fault_net < 0 this is the good machine: it fills
- * gout[T][n_out] and returns 0. Otherwise it compares against gout and returns the
- * detection (cycle, port) through *cycle/*port (both -1 if never detected). */
+ * gout[T][n_out]. Otherwise it compares against gout and returns the first detection
+ * through *cycle and *port (both -1 if never detected) and the number of cycles with a
+ * differing port through *mism. */
 static void run_machine(const oracle_design *d, const int32_t *order, int32_t T,
                         const uint64_t *stim, uint64_t *gout_w, const uint64_t *gout_r,
                         uint64_t *trace_w,
                         int64_t fault_net, unsigned fault_bit, unsigned fault_val,
-                        uint64_t *net, uint64_t *Q, int32_t *cycle, int32_t *port)
+                        int64_t fault_cycle, int no_drop,
+                        uint64_t *net, uint64_t *Q, int32_t *cycle, int32_t *port,
+                        uint32_t *mism)
 {
     int32_t I = d->n_in, R = d->n_reg, N = d->n_node, O = d->n_out;
-    uint64_t m1 = 0, m0 = 0;
+    int64_t fault_port = fault_net - (int64_t)(I + R + N);   /* >= 0: a port fault */
+    uint64_t m1 = 0, m0 = 0, mx = 0, fx;
     if (fault_net >= 0) {
-        if (fault_val) m1 = (uint64_t)1 << fault_bit;
+        if (fault_val >= 2) mx = (uint64_t)1 << fault_bit;   /* SEU / SET: a flip */
+        else if (fault_val) m1 = (uint64_t)1 << fault_bit;
         else           m0 = (uint64_t)1 << fault_bit;
     }
+#define FAULTY(x) ((((x) & ~m0) | m1) ^ fx)
 #define FORCE(netid) do { if ((int64_t)(netid) == fault_net) \
-                              net[netid] = (net[netid] & ~m0) | m1; } while (0)
+                              net[netid] = FAULTY(net[netid]); } while (0)
     for (int32_t r = 0; r < R; r++) Q[r] = 0;
-    *cycle = -1; *port = -1;
+    *cycle = -1; *port = -1; *mism = 0;
     for (int32_t t = 0; t < T; t++) {
+        fx = (int64_t)t == fault_cycle ? mx : 0;   /* the flip acts in its own cycle only */
         for (int32_t i = 0; i < I; i++) {
             net[i] = stim[(size_t)t * I + i] & mask_of(d->in_w[i]);
             FORCE(i);
@@ -177,16 +197,25 @@ static void run_machine(const oracle_design *d, const int32_t *order, int32_t T,
         if (fault_net < 0) {
             for (int32_t o = 0; o < O; o++) gout_w[(size_t)t * O + o] = net[d->out[o]];
         } else {
+            int differs = 0;
             for (int32_t o = 0; o < O; o++) {
-                if (net[d->out[o]] != gout_r[(size_t)t * O + o]) {
-                    *cycle = t; *port = o;
-                    return;
+                uint64_t seen = net[d->out[o]];
+                if ((int64_t)o == fault_port) seen = FAULTY(seen);   /* the port's virtual node */
+                if (seen != gout_r[(size_t)t * O + o]) {
+                    if (*cycle < 0) { *cycle = t; *port = o; }
+                    differs = 1;
+                    break;
                 }
+            }
+            if (differs) {
+                ++*mism;
+                if (!no_drop) return;
             }
         }
         for (int32_t r = 0; r < R; r++) Q[r] = net[d->reg_d[r]] & mask_of(d->reg_w[r]);
     }
 #undef FORCE
+#undef FAULTY
 }
 
 static size_t n_nets(const oracle_design *d) { return (size_t)d->n_in + d->n_reg + d->n_node; }
@@ -201,7 +230,8 @@ int oracle_good_run(const oracle_design *d, int32_t T, const uint64_t *stim, uin
     uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
     uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
     int32_t cy, po;
-    run_machine(d, order, T, stim, gout, NULL, trace, -1, 0, 0, net, Q, &cy, &po);
+    uint32_t mi;
+    run_machine(d, order, T, stim, gout, NULL, trace, -1, 0, 0, -1, 0, net, Q, &cy, &po, &mi);
     free(order); free(net); free(Q);
     return 0;
 }
@@ -217,9 +247,33 @@ int oracle_fault_sim(const oracle_design *d, int32_t T, const uint64_t *stim,
     if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
     uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
     uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
+    uint32_t mi;
     for (int32_t f = 0; f < F; f++) {
         run_machine(d, order, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fval[f],
-                    net, Q, &cycle[f], &port[f]);
+                    -1, 0, net, Q, &cycle[f], &port[f], &mi);
+        detected[f] = cycle[f] >= 0 ? 1 : 0;
+    }
+    free(order); free(net); free(Q);
+    return 0;
+}
+
+/* The same with a fault kind per fault (0 SA0, 1 SA1, 2 SEU, 3 SET; fcycle = the cycle
+ * of a flip), port faults (site n_net + o) and the no-drop mode; mism[f] = cycles in
+ * which some port differs (with dropping: 1 for a detected fault). Returns 0 or -1. */
+int oracle_fault_sim_ex(const oracle_design *d, int32_t T, const uint64_t *stim,
+                        const uint64_t *gout, int32_t F, const uint32_t *fnet,
+                        const uint8_t *fbit, const uint8_t *fkind, const uint32_t *fcycle,
+                        int32_t no_drop, uint8_t *detected, int32_t *cycle, int32_t *port,
+                        uint32_t *mism)
+{
+    int32_t *order = malloc(sizeof(int32_t) * ((size_t)d->n_node + 1));
+    if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
+    uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
+    uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
+    for (int32_t f = 0; f < F; f++) {
+        int64_t fc = fkind[f] >= 2 ? (int64_t)fcycle[f] : -1;
+        run_machine(d, order, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fkind[f],
+                    fc, no_drop, net, Q, &cycle[f], &port[f], &mism[f]);
         detected[f] = cycle[f] >= 0 ? 1 : 0;
     }
     free(order); free(net); free(Q);

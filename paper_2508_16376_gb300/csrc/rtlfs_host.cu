@@ -81,8 +81,9 @@ struct Design {
     uint32_t T = 0;
     bool has_stim = false;
     DBuf<uint64_t> d_stim;
-    std::vector<uint32_t> f_site;     // internal ids
-    std::vector<uint8_t> f_bit, f_val;
+    std::vector<uint32_t> f_site;     // internal ids (a port fault: the port's driver net)
+    std::vector<uint8_t> f_bit, f_val;   // f_val: fault kind FK_*
+    std::vector<uint32_t> f_port, f_t0;  // output port of a port fault (NO_PORT); flip cycle
     // good trace
     DBuf<uint64_t> d_rows, d_gcol;
     bool trace_valid = false;
@@ -136,7 +137,8 @@ struct rtlfs_ctx {
     bool faults_dirty = true;
     uint32_t F = 0;
     std::vector<uint32_t> f_first;    // first global fault id of each design
-    DBuf<uint32_t> d_site;
+    DBuf<uint32_t> d_site, d_fport, d_ft0, d_mism;
+    bool mism_valid = false;           // d_mism holds the counts of the last run (no-drop)
     DBuf<uint8_t> d_bit, d_val, d_det;
     DBuf<uint16_t> d_fdesign;
     DBuf<int32_t> d_cycle, d_port;
@@ -677,7 +679,7 @@ int enqueue_good(rtlfs_ctx *ctx) {
 
 int build_faults(rtlfs_ctx *ctx) {
     if (!ctx->faults_dirty) return RTLFS_OK;
-    std::vector<uint32_t> site;
+    std::vector<uint32_t> site, port, t0;
     std::vector<uint8_t> bit, val;
     std::vector<uint16_t> des;
     ctx->f_first.clear();
@@ -687,6 +689,8 @@ int build_faults(rtlfs_ctx *ctx) {
         site.insert(site.end(), D.f_site.begin(), D.f_site.end());
         bit.insert(bit.end(), D.f_bit.begin(), D.f_bit.end());
         val.insert(val.end(), D.f_val.begin(), D.f_val.end());
+        port.insert(port.end(), D.f_port.begin(), D.f_port.end());
+        t0.insert(t0.end(), D.f_t0.begin(), D.f_t0.end());
         des.insert(des.end(), D.f_site.size(), (uint16_t)i);
     }
     ctx->f_first.push_back((uint32_t)site.size());
@@ -694,6 +698,10 @@ int build_faults(rtlfs_ctx *ctx) {
     CU(ctx->d_site.upload(site));
     CU(ctx->d_bit.upload(bit));
     CU(ctx->d_val.upload(val));
+    CU(ctx->d_fport.upload(port));
+    CU(ctx->d_ft0.upload(t0));
+    CU(ctx->d_mism.reserve(ctx->F));
+    ctx->mism_valid = false;
     CU(ctx->d_fdesign.upload(des));
     CU(ctx->d_cycle.reserve(ctx->F));
     CU(ctx->d_port.reserve(ctx->F));
@@ -719,6 +727,8 @@ DevFaults dev_faults(rtlfs_ctx *ctx) {
     DevFaults f{};
     f.F = ctx->F;
     f.site = ctx->d_site.p; f.bit = ctx->d_bit.p; f.val = ctx->d_val.p; f.design = ctx->d_fdesign.p;
+    f.port = ctx->d_fport.p; f.t0 = ctx->d_ft0.p;
+    f.mism = nullptr;   // drop at first detection unless the run asks otherwise
     f.res_cycle = ctx->d_cycle.p; f.res_port = ctx->d_port.p; f.res_det = ctx->d_det.p;
     f.load = ctx->d_load.p;
     return f;
@@ -790,6 +800,50 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b) {
 }  // namespace
 
 // ---- ABI ------------------------------------------------------------------------------
+
+namespace {
+
+// Validate one fault (caller numbering; ids n_net + o are output ports) and convert it to
+// the device form. kind: RTLFS_FAULT_*.
+int convert_fault(rtlfs_ctx *ctx, const Design &D, uint32_t i, uint32_t net, uint32_t bit, uint32_t kind,
+                  uint32_t cycle, uint32_t *site, uint8_t *b, uint8_t *v, uint32_t *port, uint32_t *t0) {
+    if (net >= D.n_net + D.O) return fail(ctx, RTLFS_E_ARG, "fault %u: net out of range", i);
+    const bool is_port = net >= D.n_net;
+    const uint32_t in = is_port ? D.out_net[net - D.n_net] : D.ext2int[net];
+    if (bit >= D.net_w[in]) return fail(ctx, RTLFS_E_ARG, "fault %u: bit beyond net width", i);
+    const bool is_reg = !is_port && in >= D.I && in < D.I + D.R;
+    if (kind > RTLFS_FAULT_SET) return fail(ctx, RTLFS_E_ARG, "fault %u: unknown fault kind", i);
+    if (kind == RTLFS_FAULT_SEU && !is_reg) return fail(ctx, RTLFS_E_ARG, "fault %u: an SEU site must be a register", i);
+    if (kind == RTLFS_FAULT_SET && is_reg) return fail(ctx, RTLFS_E_ARG, "fault %u: a flip of a register is an SEU", i);
+    *site = in;
+    *b = (uint8_t)bit;
+    *v = (uint8_t)(kind <= RTLFS_FAULT_SA1 ? kind : FK_FLIP);
+    *port = is_port ? net - D.n_net : NO_PORT;
+    *t0 = kind <= RTLFS_FAULT_SA1 ? 0u : cycle;
+    return RTLFS_OK;
+}
+
+template <typename Get>
+int set_faults_impl(rtlfs_ctx *ctx, uint32_t design_id, uint32_t n_faults, bool null_list, Get get) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (design_id >= ctx->designs.size()) return fail(ctx, RTLFS_E_ARG, "bad design id");
+    if (n_faults && null_list) return fail(ctx, RTLFS_E_ARG, "null faults");
+    Design &D = *ctx->designs[design_id];
+    std::vector<uint32_t> s(n_faults), port(n_faults), t0(n_faults);
+    std::vector<uint8_t> b(n_faults), v(n_faults);
+    for (uint32_t i = 0; i < n_faults; ++i) {
+        uint32_t net, bit, kind, cycle;
+        int rc = get(i, &net, &bit, &kind, &cycle);
+        if (rc == RTLFS_OK) rc = convert_fault(ctx, D, i, net, bit, kind, cycle, &s[i], &b[i], &v[i], &port[i], &t0[i]);
+        if (rc != RTLFS_OK) return rc;
+    }
+    D.f_site.swap(s); D.f_bit.swap(b); D.f_val.swap(v); D.f_port.swap(port); D.f_t0.swap(t0);
+    ctx->faults_dirty = true;
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -892,23 +946,33 @@ int rtlfs_set_stimulus(rtlfs_ctx *ctx, uint32_t design_id, const uint64_t *input
 }
 
 int rtlfs_set_faults(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults, uint32_t n_faults) {
+    return set_faults_impl(ctx, design_id, n_faults, faults == nullptr,
+                           [&](uint32_t i, uint32_t *net, uint32_t *bit, uint32_t *kind, uint32_t *cycle) {
+                               const rtlfs_fault &x = faults[i];
+                               if (x.stuck > 1) return fail(ctx, RTLFS_E_ARG, "fault %u: stuck value must be 0 or 1", i);
+                               *net = x.net; *bit = x.bit; *kind = x.stuck; *cycle = 0;
+                               return (int)RTLFS_OK;
+                           });
+}
+
+int rtlfs_set_faults_ex(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault_ex *faults, uint32_t n_faults) {
+    return set_faults_impl(ctx, design_id, n_faults, faults == nullptr,
+                           [&](uint32_t i, uint32_t *net, uint32_t *bit, uint32_t *kind, uint32_t *cycle) {
+                               const rtlfs_fault_ex &x = faults[i];
+                               *net = x.net; *bit = x.bit; *kind = x.kind; *cycle = x.cycle;
+                               return (int)RTLFS_OK;
+                           });
+}
+
+int rtlfs_mismatch_counts(rtlfs_ctx *ctx, uint32_t design_id, uint32_t *out) {
     if (!ctx) return RTLFS_E_ARG;
     if (design_id >= ctx->designs.size()) return fail(ctx, RTLFS_E_ARG, "bad design id");
-    if (n_faults && !faults) return fail(ctx, RTLFS_E_ARG, "null faults");
-    Design &D = *ctx->designs[design_id];
-    std::vector<uint32_t> s(n_faults);
-    std::vector<uint8_t> b(n_faults), v(n_faults);
-    for (uint32_t i = 0; i < n_faults; ++i) {
-        const rtlfs_fault &x = faults[i];
-        if (x.net >= D.n_net) return fail(ctx, RTLFS_E_ARG, "fault %u: net out of range", i);
-        const uint32_t in = D.ext2int[x.net];
-        if (x.bit >= D.net_w[in]) return fail(ctx, RTLFS_E_ARG, "fault %u: bit beyond net width", i);
-        if (x.stuck > 1) return fail(ctx, RTLFS_E_ARG, "fault %u: stuck value must be 0 or 1", i);
-        s[i] = in; b[i] = x.bit; v[i] = x.stuck;
-    }
-    D.f_site.swap(s); D.f_bit.swap(b); D.f_val.swap(v);
-    ctx->faults_dirty = true;
-    ctx->err.clear();
+    if (!ctx->mism_valid || ctx->faults_dirty || ctx->f_first.size() != ctx->designs.size() + 1)
+        return fail(ctx, RTLFS_E_STATE, "no no-drop run since the fault lists were set");
+    const uint32_t first = ctx->f_first[design_id], n = ctx->f_first[design_id + 1] - first;
+    if (n && !out) return fail(ctx, RTLFS_E_ARG, "null output");
+    CU(cudaSetDevice(ctx->device));
+    if (n) CU(cudaMemcpy(out, ctx->d_mism.p + first, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
     return RTLFS_OK;
 }
 
@@ -976,6 +1040,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     const auto t_host1 = std::chrono::steady_clock::now();
 
     DevFaults f = dev_faults(ctx);
+    const bool nodrop = o.no_drop != 0;
+    if (nodrop) f.mism = ctx->d_mism.p;
     Queues ql{};
     ql.light_order = ctx->d_order.p + n_heavy;
     ql.n_light = F - n_heavy;
@@ -1058,6 +1124,12 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         uint32_t *prom_total = c32 + 3 * nw, *n_light0 = c32 + 3 * nw + 1, *zero = c32 + 3 * nw + 2;
         CU(cudaEventRecord(ev[0], ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
+        if (nodrop && F) {   // results are written at first detection; the rest stay undetected
+            CU(cudaMemsetAsync(ctx->d_mism.p, 0, (size_t)F * sizeof(uint32_t), ctx->s_main));
+            CU(cudaMemsetAsync(ctx->d_det.p, 0, (size_t)F, ctx->s_main));
+            CU(cudaMemsetAsync(ctx->d_cycle.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
+            CU(cudaMemsetAsync(ctx->d_port.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
+        }
         CU(cudaMemsetAsync(c32, 0, (3 * (size_t)nw + 4) * sizeof(uint32_t), ctx->s_main));
         CU(cudaMemsetAsync(c64, 0, (3 * (size_t)nw + 1) * sizeof(unsigned long long), ctx->s_main));
         CU(cudaMemcpyAsync(prom_total, ctx->p_small + 10, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
@@ -1176,6 +1248,12 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         launches = 0;
         CU(cudaEventRecord(ev[0], ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
+        if (nodrop && F) {   // results are written at first detection; the rest stay undetected
+            CU(cudaMemsetAsync(ctx->d_mism.p, 0, (size_t)F * sizeof(uint32_t), ctx->s_main));
+            CU(cudaMemsetAsync(ctx->d_det.p, 0, (size_t)F, ctx->s_main));
+            CU(cudaMemsetAsync(ctx->d_cycle.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
+            CU(cudaMemsetAsync(ctx->d_port.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
+        }
         CU(cudaMemcpyAsync(ctx->d_counters.p, cinit, 4 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
         if (F) CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
         int r2 = launch_good(ctx, &launches);
@@ -1222,7 +1300,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         // Everything the captured work depends on by address or size.
         std::vector<uint64_t> key = {F, n_heavy, ql.n_light, (uint64_t)lcap, (uint64_t)lblock,
                                      (uint64_t)lgrid, (uint64_t)hblock, (uint64_t)hgrid,
-                                     (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W};
+                                     (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W,
+                                     (uint64_t)nodrop};
         const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p,
                               ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
                               ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,
@@ -1277,6 +1356,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     const unsigned long long *heads = ctx->p_small;
     const uint32_t *cnts = reinterpret_cast<const uint32_t *>(ctx->p_small + 8);
     for (Design *D : ctx->designs) D->trace_valid = true;
+    ctx->mism_valid = nodrop;
 
     // Scatter results and counters.
     rtlfs_stats &st = ctx->stats;
@@ -1351,6 +1431,7 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out) {
     if (rc != RTLFS_OK) return rc;
     CU(cudaEventRecord(ev[1], ctx->s_main));
     DevFaults f = dev_faults(ctx);
+    ctx->mism_valid = false;
     uint32_t launches = 2 + (uint32_t)ctx->designs.size();
     // per-thread scratch, waves sized to a fixed memory budget
     const size_t budget = (size_t)8 << 30;

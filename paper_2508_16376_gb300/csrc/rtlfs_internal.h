@@ -82,11 +82,19 @@ constexpr uint32_t CL_SELF = 1u << 29;
 constexpr uint32_t CL_MAX = 16;   // largest cluster (non-portable size on sm_103a)
 
 // All faults of all designs, concatenated in design order.
+// Fault kinds (DevFaults.val): stuck-at 0, stuck-at 1, and a flip of the bit during one
+// cycle (t0): a single-event upset on a register, a single-event transient on a net.
+constexpr uint32_t FK_SA0 = 0, FK_SA1 = 1, FK_FLIP = 2;
+
 struct DevFaults {
     uint32_t F;
-    const uint32_t *site;       // internal net id
+    const uint32_t *site;       // internal net id (a port fault: the port's driver net)
     const uint8_t  *bit;
-    const uint8_t  *val;
+    const uint8_t  *val;        // kind: FK_SA0, FK_SA1, FK_FLIP
+    const uint32_t *port;       // output port of a port fault, NO_PORT for a net fault
+    const uint32_t *t0;         // cycle of an FK_FLIP fault
+    uint32_t *mism;             // no-drop mode: cycles with a differing output per fault;
+                                // null = drop each fault at its first detection
     const uint16_t *design;     // design index of each fault
     int32_t  *res_cycle;
     int32_t  *res_port;

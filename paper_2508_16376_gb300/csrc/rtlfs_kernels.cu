@@ -55,9 +55,29 @@ __device__ __forceinline__ uint64_t eval_op(uint4 d, uint64_t a, uint64_t b, uin
     return r & wmask(meta_w(m));
 }
 
-// Stuck-at fault function: force bit `bm` (a one-hot mask) to `sv`.
-__device__ __forceinline__ uint64_t force_bit(uint64_t x, uint64_t bm, bool sv) {
-    return sv ? (x | bm) : (x & ~bm);
+// The fault function at a fault's site (Sec. IV-A: applied wherever the site's value is
+// produced; a virtual function in the paper, a switch on the kind here): stuck-at 0 or 1
+// forces the bit in every cycle; a transient flip (an SEU on a register, an SET on an
+// input or node net) inverts it during cycle t0 only. A port fault (port != NO_PORT) acts
+// on what one output port observes of the site net and on nothing else.
+struct FaultSite {
+    uint32_t site, port, kind, t0;
+    uint64_t bm;   // one-hot mask of the faulted bit
+    __device__ __forceinline__ uint64_t apply(uint64_t v, uint32_t t) const {
+        return kind == FK_SA0 ? (v & ~bm) : kind == FK_SA1 ? (v | bm) : (t == t0 ? v ^ bm : v);
+    }
+    // whether the fault function changes anything in cycle t (a stuck-at fault: always)
+    __device__ __forceinline__ bool acts(uint32_t t) const { return kind != FK_FLIP || t == t0; }
+};
+
+__device__ __forceinline__ FaultSite load_fault(const DevFaults &f, uint32_t fid) {
+    FaultSite s;
+    s.site = f.site[fid];
+    s.kind = f.val[fid];
+    s.bm = 1ull << f.bit[fid];
+    s.port = f.port ? f.port[fid] : NO_PORT;
+    s.t0 = f.t0 ? f.t0[fid] : 0u;
+    return s;
 }
 
 // ===================================================================================
@@ -399,13 +419,14 @@ __global__ void activation_kernel(const DevDesign *__restrict__ designs, DevFaul
     const DevDesign &D = designs[f.design[fid]];
     const uint32_t T = D.T, te = min(t1, T);
     const uint32_t site = f.site[fid], bit = f.bit[fid];
-    const uint64_t sv = f.val[fid];
+    const uint64_t sv = f.val[fid];   // a stuck-at fault acts where the bit differs from it
+    const uint32_t tf = f.t0 ? f.t0[fid] : 0u;   // a flip acts in its own cycle only
     const uint64_t *col = D.gcol + (size_t)site * T;
     uint64_t *out = act + (size_t)fid * f.act_stride;
     for (uint32_t tw = t0; tw < te; tw += 64) {
         const uint32_t ta = tw + lane, tb = tw + 32 + lane;
-        const bool a = ta < te && ((__ldg(col + ta) >> bit) & 1ull) != sv;
-        const bool b = tb < te && ((__ldg(col + tb) >> bit) & 1ull) != sv;
+        const bool a = ta < te && (sv == FK_FLIP ? ta == tf : ((__ldg(col + ta) >> bit) & 1ull) != sv);
+        const bool b = tb < te && (sv == FK_FLIP ? tb == tf : ((__ldg(col + tb) >> bit) & 1ull) != sv);
         const uint32_t lo = __ballot_sync(0xFFFFFFFFu, a), hi = __ballot_sync(0xFFFFFFFFu, b);
         if (lane == 0) out[tw >> 6] = ((uint64_t)hi << 32) | lo;
     }
@@ -422,250 +443,6 @@ __device__ __forceinline__ uint32_t next_active(const uint64_t *__restrict__ fac
         t = (t | 63u) + 1;
     }
     return tend;
-}
-
-// ===================================================================================
-// Light kernel: one lane per fault, persistent, lanes take faults from a global queue
-// (atomic counter) as they finish -- dynamic balancing of the many low-load faults.
-//
-// Per fault and cycle the lane keeps, in its own slice of shared memory:
-//   register diffs of the start of the cycle (reg, faulty Q) and of the next cycle,
-//   the nets whose faulty value differs this cycle (net, value), sorted by net id,
-//   a min-heap of node indices still to evaluate (topological order = index order).
-// A cycle: seed the diff with the register diffs (and the forced site if it is an input
-// or register), push the site node, then pop nodes in index order, evaluate each with
-// faulty operands (diff value, else the good trace), force the site bit, keep the result
-// if it differs from the good value and push its fan-out. The lowest output port among
-// differing nets detects the fault; register diffs for the next cycle are collected as
-// nets are kept (the latch, fused into the cycle). With no register diff left, only the
-// site can make the machines differ again, so the lane skips to the next cycle where
-// the site bit's good value differs from the stuck value. Any capacity overflow hands
-// the fault, with its start-of-cycle state, to the heavy kernel.
-// ===================================================================================
-template <int KR, int KD, int KH>
-__global__ void __launch_bounds__(256, 1)
-light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
-    extern __shared__ __align__(16) unsigned char lsm[];
-    const uint32_t B = blockDim.x, tx = threadIdx.x;
-    uint64_t *rv = reinterpret_cast<uint64_t *>(lsm);           // [2][KR][B]
-    uint64_t *dv = rv + 2 * KR * B;                              // [KD][B]
-    uint32_t *rr = reinterpret_cast<uint32_t *>(dv + KD * B);   // [2][KR][B]
-    uint32_t *dn = rr + 2 * KR * B;                              // [KD][B]
-    uint32_t *hp = dn + KD * B;                                  // [KH][B]
-#define RV(bf, k) rv[((bf) * KR + (k)) * B + tx]
-#define RR(bf, k) rr[((bf) * KR + (k)) * B + tx]
-#define DV(k) dv[(k) * B + tx]
-#define DN(k) dn[(k) * B + tx]
-#define HP(k) hp[(k) * B + tx]
-
-    for (;;) {
-        const unsigned long long qi = atomicAdd(q.light_head, 1ull);
-        if (qi >= q.n_light) break;
-        const uint32_t fid = q.light_order[qi];
-        const DevDesign &D = designs[f.design[fid]];
-        const uint32_t I = D.I, IR = D.I + D.R, T = D.T;
-        const uint64_t *__restrict__ gcol = D.gcol;
-        const uint4 *__restrict__ netinfo = D.netinfo;
-        const uint4 *__restrict__ desc = D.desc;
-        const uint32_t *__restrict__ fo_idx = D.fo_idx;
-        const uint32_t *__restrict__ dreg_off = D.dreg_off;
-        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
-        const uint32_t site = f.site[fid];
-        const uint32_t bit = f.bit[fid];
-        const bool sv = f.val[fid] != 0;
-        const uint64_t bm = 1ull << bit;
-        const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
-        const uint32_t site_node = site >= IR ? site - IR : 0xFFFFFFFFu;
-
-        uint32_t t = 0, nreg = 0, cur = 0;
-        uint64_t load = 0;
-        int status = 0;                 // 1 detected, 2 promoted, 3 budget
-        int32_t det_cycle = -1, det_port = -1;
-
-        for (;;) {
-            if (nreg == 0) {
-                // Skip quiescent cycles: nothing differs unless the site bit is activated.
-                // With the activation bitplane, 64 cycles per load; else four cycles per step.
-                const uint64_t want = sv ? bm : 0ull;   // site bit equal to the stuck value: quiescent
-                if (f.act) {
-                    t = next_active(f.act + (size_t)fid * f.act_stride, t, T);
-                } else {
-                    while (t + 4 <= T) {
-                        const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
-                        const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
-                        if ((g0 & bm) != want) break;
-                        if ((g1 & bm) != want) { t += 1; break; }
-                        if ((g2 & bm) != want) { t += 2; break; }
-                        if ((g3 & bm) != want) { t += 3; break; }
-                        t += 4;
-                    }
-                    if (t + 4 > T) {
-                        while (t < T && (__ldg(scol + t) & bm) == want) ++t;
-                    }
-                }
-                if (t >= T) break;
-            }
-            const uint32_t nb = cur ^ 1u;
-            uint32_t nd = 0, nh = 0, nreg_new = 0, minport = NI_NO_PORT;
-            uint64_t filter = 0;
-            bool ovf = false;
-            const uint64_t load_at_cycle_start = load;   // the heavy kernel redoes a promoted cycle
-
-            auto heap_push = [&](uint32_t x) {
-                if (nh >= (uint32_t)KH) { ovf = true; return; }
-                uint32_t i = nh++;
-                while (i > 0) {
-                    const uint32_t p = (i - 1) >> 1;
-                    const uint32_t hpv = HP(p);
-                    if (hpv <= x) break;
-                    HP(i) = hpv;
-                    i = p;
-                }
-                HP(i) = x;
-            };
-            auto heap_pop = [&]() -> uint32_t {
-                const uint32_t top = HP(0);
-                const uint32_t x = HP(--nh);
-                uint32_t i = 0;
-                for (;;) {
-                    uint32_t c = 2 * i + 1;
-                    if (c >= nh) break;
-                    uint32_t cv = HP(c);
-                    if (c + 1 < nh) {
-                        const uint32_t cv2 = HP(c + 1);
-                        if (cv2 < cv) { cv = cv2; ++c; }
-                    }
-                    if (x <= cv) break;
-                    HP(i) = cv;
-                    i = c;
-                }
-                if (nh > 0) HP(i) = x;
-                return top;
-            };
-            // Keep net (faulty v, good g, record ni): diff entry, detection, fan-out, latch.
-            auto add_diff = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
-                if (nd >= (uint32_t)KD) { ovf = true; return; }
-                DN(nd) = net;
-                DV(nd) = v;
-                ++nd;
-                filter |= 1ull << (net & 63u);
-                const uint32_t p = ni_port(ni.w);
-                minport = p < minport ? p : minport;
-                if (ni.y - ni.x > (uint32_t)KH) { ovf = true; return; }
-                for (uint32_t e = ni.x; e < ni.y; e += 4) {
-                    // four independent loads in flight, then the pushes
-                    const uint32_t c0 = __ldg(fo_idx + e);
-                    const uint32_t c1 = e + 1 < ni.y ? __ldg(fo_idx + e + 1) : 0xFFFFFFFFu;
-                    const uint32_t c2 = e + 2 < ni.y ? __ldg(fo_idx + e + 2) : 0xFFFFFFFFu;
-                    const uint32_t c3 = e + 3 < ni.y ? __ldg(fo_idx + e + 3) : 0xFFFFFFFFu;
-                    heap_push(c0);
-                    if (c1 != 0xFFFFFFFFu) heap_push(c1);
-                    if (c2 != 0xFFFFFFFFu) heap_push(c2);
-                    if (c3 != 0xFFFFFFFFu) heap_push(c3);
-                }
-                uint32_t nr = ni_nreg(ni.w);
-                if (nr) {
-                    if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
-                    for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                        const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
-                        const uint32_t r = rec & 0x1FFFFFFu;
-                        const uint64_t wm = wmask(rec >> 25);
-                        const uint64_t qv = v & wm;
-                        if (qv != (g & wm)) {
-                            if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
-                            RR(nb, nreg_new) = r;
-                            RV(nb, nreg_new) = qv;
-                            ++nreg_new;
-                        }
-                    }
-                }
-            };
-            auto lookup = [&](uint32_t x) -> uint64_t {
-                if ((filter >> (x & 63u)) & 1ull) {
-                    for (uint32_t k = 0; k < nd; ++k)
-                        if (DN(k) == x) return DV(k);
-                }
-                return __ldg(gcol + (size_t)x * T + t);
-            };
-
-            bool site_seeded = false;
-            for (uint32_t k = 0; k < nreg && !ovf; ++k) {
-                const uint32_t net = I + RR(cur, k);
-                uint64_t qv = RV(cur, k);
-                if (net == site) { qv = force_bit(qv, bm, sv); site_seeded = true; }
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (qv != g) add_diff(net, qv, g, __ldg(netinfo + net));
-            }
-            if (site < IR && !site_seeded && !ovf) {
-                const uint64_t g = __ldg(scol + t);
-                const uint64_t fv = force_bit(g, bm, sv);
-                if (fv != g) add_diff(site, fv, g, __ldg(netinfo + site));
-            }
-            if (site_node != 0xFFFFFFFFu && !ovf) heap_push(site_node);
-            uint32_t last = 0xFFFFFFFFu;
-            while (nh > 0 && !ovf) {
-                const uint32_t n = heap_pop();
-                if (n == last) continue;
-                last = n;
-                const uint32_t net = IR + n;
-                // independent loads first: descriptor, net record, good value
-                const uint4 d = __ldg(desc + n);
-                const uint4 ni = __ldg(netinfo + net);
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                const uint32_t op = meta_op(d.w);
-                const int no = n_operands(op);
-                uint64_t a = 0, b = 0, c = 0;
-                if (no >= 1) a = lookup(d.x);
-                if (no >= 2) b = lookup(d.y);
-                if (no >= 3) c = lookup(d.z);
-                uint64_t v = eval_op(d, a, b, c);
-                if (n == site_node) v = force_bit(v, bm, sv);
-                ++load;
-                if (v != g) add_diff(net, v, g, ni);
-            }
-            if (ovf) {
-                const uint32_t p = atomicAdd(q.heavy_count, 1u);
-                if (p < q.heavy_cap) {
-                    HeavyItem &h = q.heavy_items[p];
-                    h.fault = fid;
-                    h.t = t;
-                    h.nreg = nreg;
-                    for (uint32_t k = 0; k < nreg; ++k) {
-                        h.reg_r[k] = RR(cur, k);
-                        h.reg_v[k] = RV(cur, k);
-                    }
-                }
-                load = load_at_cycle_start;
-                status = 2;
-                break;
-            }
-            if (minport != NI_NO_PORT) {
-                det_cycle = (int32_t)t;
-                det_port = (int32_t)minport;
-                status = 1;
-                break;
-            }
-            cur = nb;
-            nreg = nreg_new;
-            if (++t >= T) break;
-            if (q.fault_budget && load > q.fault_budget) { status = 3; break; }
-        }
-        f.load[fid] = load;
-        if (status != 2) {
-            f.res_det[fid] = status == 1 ? 1 : status == 3 ? 255 : 0;
-            f.res_cycle[fid] = det_cycle;
-            f.res_port[fid] = det_port;
-            if (status == 3) atomicAdd(q.budget_hit, 1ull);
-        }
-        // t is the first cycle not completed (detection cycle counts as simulated)
-        atomicAdd(q.counters + 0, (unsigned long long)load);
-        atomicAdd(q.counters + 1, (unsigned long long)(status == 1 ? t + 1 : t));
-    }
-#undef RV
-#undef RR
-#undef DV
-#undef DN
-#undef HP
 }
 
 // ===================================================================================
@@ -756,6 +533,7 @@ struct HeavyRun {
     uint32_t cur;      // out: the half of regR/regV that holds the live register diffs
     int status;        // 0 alive at tend, 1 detected at t, 3 over the load budget
     int32_t det_cycle, det_port;
+    uint32_t mism;     // no-drop mode: cycles of this run with a differing output
 };
 
 // Simulate fault fid from cycle r.t until it is detected, exceeds the load budget or
@@ -776,17 +554,36 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
     const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
     const uint32_t *__restrict__ dreg_off = D.dreg_off;
     const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
-    const uint32_t site = f.site[fid];
+    const FaultSite fs = load_fault(f, fid);
+    const uint32_t site = fs.site;
     const uint32_t bit = f.bit[fid];
-    const bool sv = f.val[fid] != 0;
-    const uint64_t bmask = 1ull << bit;
     const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
     uint32_t *const bm = sm.bm, *const cnt = sm.cnt, *const dbm = sm.dbm;
     unsigned long long *const lvm = sm.lvm;
     const uint32_t nlw = sm.nlw;
-    uint32_t t = r.t, nreg = r.nreg, cur = 0;
+    const bool nodrop = f.mism != nullptr;
+    bool seen = nodrop && f.res_det[fid] == 1;   // no-drop: first detection already recorded
+    uint32_t t = r.t, nreg = r.nreg, cur = 0, mism = 0;
     int status = 0;
     int32_t det_cycle = -1, det_port = -1;
+    // A detection at cycle t on `port` (uniform across the CTA): stop (dropping), or
+    // record the first one and count.
+    auto detect = [&](uint32_t port) -> bool {
+        if (!nodrop) {
+            det_cycle = (int32_t)t;
+            det_port = (int32_t)port;
+            status = 1;
+            return true;
+        }
+        if (!seen && tid == 0) {
+            f.res_det[fid] = 1;
+            f.res_cycle[fid] = (int32_t)t;
+            f.res_port[fid] = (int32_t)port;
+        }
+        seen = true;
+        ++mism;
+        return false;
+    };
 
     // Consumer node c (at level lv) becomes dirty.
     auto mark = [&](uint32_t c, uint32_t lv) {
@@ -851,23 +648,37 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
     };
 
     for (;;) {
-        if (nreg == 0) {   // nothing latched: jump to the next cycle the site is active
-            if (warp == 0 && f.act) {
-                if (lane == 0) V.t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
-            } else if (warp == 0) {
-                uint32_t found = tend;
-                for (uint32_t tt = t; tt < tend; tt += 32) {
-                    const uint32_t u = tt + lane;
-                    bool act = false;
-                    if (u < tend) act = ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)sv;
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, act);
-                    if (bal) { found = tt + __ffs(bal) - 1; break; }
+        if (nreg == 0) {   // nothing latched: jump to the next cycle the fault acts by itself
+            if (fs.kind == FK_FLIP) {
+                t = t <= fs.t0 ? min(fs.t0, tend) : tend;
+            } else {
+                if (warp == 0 && f.act) {
+                    if (lane == 0) V.t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
+                } else if (warp == 0) {
+                    uint32_t found = tend;
+                    for (uint32_t tt = t; tt < tend; tt += 32) {
+                        const uint32_t u = tt + lane;
+                        bool act = false;
+                        if (u < tend) act = ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)fs.kind;
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, act);
+                        if (bal) { found = tt + __ffs(bal) - 1; break; }
+                    }
+                    if (lane == 0) V.t = found;
                 }
-                if (lane == 0) V.t = found;
+                __syncthreads();
+                t = V.t;
             }
-            __syncthreads();
-            t = V.t;
             if (t >= tend) break;
+            if (fs.port != NO_PORT) {
+                // a port fault changes only what its port observes of the site net: the
+                // machines differ exactly in the cycles the fault acts (virtual node evaluated)
+                if (tid == 0) V.load += 1;
+                if (detect(fs.port)) break;
+                __syncthreads();
+                if (++t >= tend) break;
+                if (budget && (f.load[fid] + V.load) > budget) { status = 3; break; }
+                continue;
+            }
         }
         const uint32_t nb = cur ^ 1u;
         if (tid == 0) { V.nreg_new = 0; V.minport = NI_NO_PORT; V.site_seeded = 0; V.nd = 0; V.nfr = 0; }
@@ -880,21 +691,21 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
             uint64_t qv = regV[cur * max_reg + k];
             const uint4 ni = __ldg(netinfo + net);
             const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-            if (net == site) { qv = force_bit(qv, bmask, sv); V.site_seeded = 1; }
+            if (net == site) { qv = fs.apply(qv, t); V.site_seeded = 1; }
             if (qv != g) { keep_value(net, qv, g, ni, nb); keep_fanout(ni); }
         }
         __syncthreads();
         if (tid == 0) {
             if (site < IR && !V.site_seeded) {   // input or register site
                 const uint64_t g = __ldg(scol + t);
-                const uint64_t fv = force_bit(g, bmask, sv);
+                const uint64_t fv = fs.apply(g, t);
                 if (fv != g) {
                     const uint4 ni = __ldg(netinfo + site);
                     keep_value(site, fv, g, ni, nb);
                     keep_fanout(ni);
                 }
             }
-            if (site >= IR) mark(site - IR, __ldg(D.node_level + site - IR));   // node site
+            if (site >= IR && fs.acts(t)) mark(site - IR, __ldg(D.node_level + site - IR));   // node site
         }
         __syncthreads();
         expand();
@@ -925,7 +736,7 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
             if (no >= 2) b = lookup(d.y);
             if (no >= 3) c = lookup(d.z);
             uint64_t v = eval_op(d, a, b, c);
-            if (net == site) v = force_bit(v, bmask, sv);
+            if (net == site) v = fs.apply(v, t);
             ++my_load;
             if (v != g) {
                 keep_value(net, v, g, ni, nb);
@@ -993,12 +804,7 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
         } else {
             for (uint32_t i = tid; i < sm.nwd; i += B) dbm[i] = 0;
         }
-        if (V.minport != NI_NO_PORT) {
-            det_cycle = (int32_t)t;
-            det_port = (int32_t)V.minport;
-            status = 1;
-            break;
-        }
+        if (V.minport != NI_NO_PORT && detect(V.minport)) break;
         nreg = V.nreg_new;
         cur = nb;
         if (++t >= tend) break;
@@ -1011,6 +817,7 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
     r.status = status;
     r.det_cycle = det_cycle;
     r.det_port = det_port;
+    r.mism = mism;
 }
 
 __global__ void __launch_bounds__(1024)
@@ -1044,14 +851,17 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         }
         if (tid == 0) V.load = 0;
         __syncthreads();
-        HeavyRun r{it.t, it.nreg, 0, 0, -1, -1};
+        HeavyRun r{it.t, it.nreg, 0, 0, -1, -1, 0};
         heavy_run_fault(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
         __syncthreads();
         if (tid == 0) {
             f.load[fid] += V.load;
-            f.res_det[fid] = r.status == 1 ? 1 : r.status == 3 ? 255 : 0;
-            f.res_cycle[fid] = r.det_cycle;
-            f.res_port[fid] = r.det_port;
+            if (f.mism) f.mism[fid] += r.mism;
+            if (!(r.status == 0 && f.mism)) {   // no-drop: a detection was recorded when it happened
+                f.res_det[fid] = r.status == 1 ? 1 : r.status == 3 ? 255 : 0;
+                f.res_cycle[fid] = r.det_cycle;
+                f.res_port[fid] = r.det_port;
+            }
             if (r.status == 3) atomicAdd(q.budget_hit, 1ull);
             atomicAdd(q.counters + 0, V.load);
             const uint32_t t_end = r.status == 1 ? r.t + 1 : min(r.t, D.T);
@@ -1100,7 +910,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         }
         if (tid == 0) V.load = 0;
         __syncthreads();
-        HeavyRun r{t_start, nreg0, 0, 0, -1, -1};
+        HeavyRun r{t_start, nreg0, 0, 0, -1, -1, 0};
         heavy_run_fault(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
         __syncthreads();
         const bool carry = r.status == 0 && tend < D.T;   // alive at the end of the window
@@ -1122,7 +932,8 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         }
         if (tid == 0) {
             f.load[fid] += V.load;
-            if (!carry) {
+            if (f.mism) f.mism[fid] += r.mism;
+            if (!carry && !(r.status == 0 && f.mism)) {
                 f.res_det[fid] = r.status == 1 ? 1 : r.status == 3 ? 255 : 0;
                 f.res_cycle[fid] = r.det_cycle;
                 f.res_port[fid] = r.det_port;
@@ -1136,24 +947,326 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
     }
 }
 
-// Windowed light kernel: the light kernel over cycles [t0, t1) of the live faults;
-// survivors carry their register diffs to the next window.
+// ===================================================================================
+// Light kernel: one lane per fault, persistent, lanes take faults from a global queue
+// (atomic counter) as they finish -- dynamic balancing of the many low-load faults.
+//
+// Per fault and cycle the lane keeps, in its own slice of shared memory:
+//   register diffs of the start of the cycle (reg, faulty Q) and of the next cycle,
+//   the nets whose faulty value differs this cycle (net, value), in the order kept,
+//   a min-heap of node indices still to evaluate (topological order = index order).
+// A cycle: seed the diff with the register diffs (and the faulted site if it is an input
+// or register), push the site node, then pop nodes in index order, evaluate each with
+// faulty operands (diff value, else the good trace), apply the fault function at the
+// site, keep the result if it differs from the good value and push its fan-out. The
+// lowest output port among differing nets detects the fault; register diffs for the next
+// cycle are collected as nets are kept (the latch, fused into the cycle). With no register
+// diff left, only the fault itself can make the machines differ again, so the lane skips
+// to the next cycle in which it acts. Any capacity overflow hands the fault, with its
+// start-of-cycle state, to the heavy kernel. The two kernels below share this per-fault
+// loop; they differ in where the faults come from and where a survivor's state goes.
+// ===================================================================================
+
+// Outcome of one light fault's run.
+struct LightRun {
+    uint32_t t;        // in: first cycle; out: first cycle not completed (see status)
+    uint32_t nreg;     // in: register diffs in half 0; out: in half `cur`
+    uint32_t cur;      // out: the half holding the live register diffs
+    int status;        // 0 alive at tend, 1 detected at t, 2 promoted at t, 3 over budget
+    int32_t det_cycle, det_port;
+    uint64_t load;     // node evaluations of this run (a promoted cycle excluded)
+    uint32_t mism;     // no-drop mode: cycles of this run with a differing output
+};
+
+// Where a light lane hands an overflowing fault.
+struct Promote {
+    HeavyItem *items;
+    uint32_t *count;
+    uint32_t cap;
+};
+
 template <int KR, int KD, int KH>
-__global__ void __launch_bounds__(256, 1)
-light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight q) {
-    extern __shared__ __align__(16) unsigned char lsm[];
+__device__ __forceinline__ void light_run_fault(const DevDesign &D, const DevFaults &f, uint32_t fid,
+                                                uint32_t tend, uint64_t budget, uint64_t load_before,
+                                                Promote prom, uint64_t *rv, uint64_t *dv, uint32_t *rr,
+                                                uint32_t *dn, uint32_t *hp, LightRun &r) {
     const uint32_t B = blockDim.x, tx = threadIdx.x;
-    uint64_t *rv = reinterpret_cast<uint64_t *>(lsm);           // [2][KR][B]
-    uint64_t *dv = rv + 2 * KR * B;                              // [KD][B]
-    uint32_t *rr = reinterpret_cast<uint32_t *>(dv + KD * B);   // [2][KR][B]
-    uint32_t *dn = rr + 2 * KR * B;                              // [KD][B]
-    uint32_t *hp = dn + KD * B;                                  // [KH][B]
 #define RV(bf, k) rv[((bf) * KR + (k)) * B + tx]
 #define RR(bf, k) rr[((bf) * KR + (k)) * B + tx]
 #define DV(k) dv[(k) * B + tx]
 #define DN(k) dn[(k) * B + tx]
 #define HP(k) hp[(k) * B + tx]
+    const uint32_t I = D.I, IR = D.I + D.R, T = D.T;
+    const uint64_t *__restrict__ gcol = D.gcol;
+    const uint4 *__restrict__ netinfo = D.netinfo;
+    const uint4 *__restrict__ desc = D.desc;
+    const uint32_t *__restrict__ fo_idx = D.fo_idx;
+    const uint32_t *__restrict__ dreg_off = D.dreg_off;
+    const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
+    const FaultSite fs = load_fault(f, fid);
+    const uint32_t site = fs.site;
+    const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
+    const uint32_t site_node = site >= IR ? site - IR : 0xFFFFFFFFu;
+    const bool nodrop = f.mism != nullptr;
+    bool seen = nodrop && f.res_det[fid] == 1;   // no-drop: first detection already recorded
 
+    uint32_t t = r.t, nreg = r.nreg, cur = 0, mism = 0;
+    uint64_t load = 0;
+    int status = 0;
+    int32_t det_cycle = -1, det_port = -1;
+    // A detection at cycle t on `port`: stop (dropping), or record the first one and count.
+    auto detect = [&](uint32_t port) -> bool {
+        if (!nodrop) {
+            det_cycle = (int32_t)t;
+            det_port = (int32_t)port;
+            status = 1;
+            return true;
+        }
+        if (!seen) {
+            f.res_det[fid] = 1;
+            f.res_cycle[fid] = (int32_t)t;
+            f.res_port[fid] = (int32_t)port;
+            seen = true;
+        }
+        ++mism;
+        return false;
+    };
+
+    for (;;) {
+        if (nreg == 0) {
+            // Nothing latched: skip to the next cycle in which the fault acts by itself.
+            // With the activation bitplane, 64 cycles per load; else four cycles per step.
+            if (fs.kind == FK_FLIP) {
+                t = t <= fs.t0 ? min(fs.t0, tend) : tend;
+            } else if (f.act) {
+                t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
+            } else {
+                const uint64_t want = fs.kind == FK_SA1 ? fs.bm : 0ull;   // quiescent: bit == stuck
+                while (t + 4 <= tend) {
+                    const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
+                    const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
+                    if ((g0 & fs.bm) != want) break;
+                    if ((g1 & fs.bm) != want) { t += 1; break; }
+                    if ((g2 & fs.bm) != want) { t += 2; break; }
+                    if ((g3 & fs.bm) != want) { t += 3; break; }
+                    t += 4;
+                }
+                if (t + 4 > tend) {
+                    while (t < tend && (__ldg(scol + t) & fs.bm) == want) ++t;
+                }
+            }
+            if (t >= tend) break;
+            if (fs.port != NO_PORT) {
+                // a port fault changes only what its port observes of the site net: the
+                // machines differ exactly in the cycles the fault acts (virtual node evaluated)
+                ++load;
+                if (detect(fs.port)) break;
+                if (++t >= tend) break;
+                if (budget && load_before + load > budget) { status = 3; break; }
+                continue;
+            }
+        }
+        const uint32_t nb = cur ^ 1u;
+        uint32_t nd = 0, nh = 0, nreg_new = 0, minport = NI_NO_PORT;
+        uint64_t filter = 0;
+        bool ovf = false;
+        const uint64_t load_at_cycle_start = load;   // the heavy kernel redoes a promoted cycle
+
+        auto heap_push = [&](uint32_t x) {
+            if (nh >= (uint32_t)KH) { ovf = true; return; }
+            uint32_t i = nh++;
+            while (i > 0) {
+                const uint32_t p = (i - 1) >> 1;
+                const uint32_t hpv = HP(p);
+                if (hpv <= x) break;
+                HP(i) = hpv;
+                i = p;
+            }
+            HP(i) = x;
+        };
+        auto heap_pop = [&]() -> uint32_t {
+            const uint32_t top = HP(0);
+            const uint32_t x = HP(--nh);
+            uint32_t i = 0;
+            for (;;) {
+                uint32_t c = 2 * i + 1;
+                if (c >= nh) break;
+                uint32_t cv = HP(c);
+                if (c + 1 < nh) {
+                    const uint32_t cv2 = HP(c + 1);
+                    if (cv2 < cv) { cv = cv2; ++c; }
+                }
+                if (x <= cv) break;
+                HP(i) = cv;
+                i = c;
+            }
+            if (nh > 0) HP(i) = x;
+            return top;
+        };
+        // Keep net (faulty v, good g, record ni): diff entry, detection, fan-out, latch.
+        auto add_diff = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
+            if (nd >= (uint32_t)KD) { ovf = true; return; }
+            DN(nd) = net;
+            DV(nd) = v;
+            ++nd;
+            filter |= 1ull << (net & 63u);
+            const uint32_t p = ni_port(ni.w);
+            minport = p < minport ? p : minport;
+            if (ni.y - ni.x > (uint32_t)KH) { ovf = true; return; }
+            for (uint32_t e = ni.x; e < ni.y; e += 4) {
+                // four independent loads in flight, then the pushes
+                const uint32_t c0 = __ldg(fo_idx + e);
+                const uint32_t c1 = e + 1 < ni.y ? __ldg(fo_idx + e + 1) : 0xFFFFFFFFu;
+                const uint32_t c2 = e + 2 < ni.y ? __ldg(fo_idx + e + 2) : 0xFFFFFFFFu;
+                const uint32_t c3 = e + 3 < ni.y ? __ldg(fo_idx + e + 3) : 0xFFFFFFFFu;
+                heap_push(c0);
+                if (c1 != 0xFFFFFFFFu) heap_push(c1);
+                if (c2 != 0xFFFFFFFFu) heap_push(c2);
+                if (c3 != 0xFFFFFFFFu) heap_push(c3);
+            }
+            uint32_t nr = ni_nreg(ni.w);
+            if (nr) {
+                if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
+                for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
+                    const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+                    const uint32_t rg = rec & 0x1FFFFFFu;
+                    const uint64_t wm = wmask(rec >> 25);
+                    const uint64_t qv = v & wm;
+                    if (qv != (g & wm)) {
+                        if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
+                        RR(nb, nreg_new) = rg;
+                        RV(nb, nreg_new) = qv;
+                        ++nreg_new;
+                    }
+                }
+            }
+        };
+        auto lookup = [&](uint32_t x) -> uint64_t {
+            if ((filter >> (x & 63u)) & 1ull) {
+                for (uint32_t k = 0; k < nd; ++k)
+                    if (DN(k) == x) return DV(k);
+            }
+            return __ldg(gcol + (size_t)x * T + t);
+        };
+
+        bool site_seeded = false;
+        for (uint32_t k = 0; k < nreg && !ovf; ++k) {
+            const uint32_t net = I + RR(cur, k);
+            uint64_t qv = RV(cur, k);
+            if (net == site) { qv = fs.apply(qv, t); site_seeded = true; }
+            const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+            if (qv != g) add_diff(net, qv, g, __ldg(netinfo + net));
+        }
+        if (site < IR && !site_seeded && !ovf) {
+            const uint64_t g = __ldg(scol + t);
+            const uint64_t fv = fs.apply(g, t);
+            if (fv != g) add_diff(site, fv, g, __ldg(netinfo + site));
+        }
+        if (site_node != 0xFFFFFFFFu && fs.acts(t) && !ovf) heap_push(site_node);
+        uint32_t last = 0xFFFFFFFFu;
+        while (nh > 0 && !ovf) {
+            const uint32_t n = heap_pop();
+            if (n == last) continue;
+            last = n;
+            const uint32_t net = IR + n;
+            // independent loads first: descriptor, net record, good value
+            const uint4 d = __ldg(desc + n);
+            const uint4 ni = __ldg(netinfo + net);
+            const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+            const uint32_t op = meta_op(d.w);
+            const int no = n_operands(op);
+            uint64_t a = 0, b = 0, c = 0;
+            if (no >= 1) a = lookup(d.x);
+            if (no >= 2) b = lookup(d.y);
+            if (no >= 3) c = lookup(d.z);
+            uint64_t v = eval_op(d, a, b, c);
+            if (n == site_node) v = fs.apply(v, t);
+            ++load;
+            if (v != g) add_diff(net, v, g, ni);
+        }
+        if (ovf) {
+            const uint32_t p = atomicAdd(prom.count, 1u);
+            if (p < prom.cap) {
+                HeavyItem &h = prom.items[p];
+                h.fault = fid;
+                h.t = t;
+                h.nreg = nreg;
+                for (uint32_t k = 0; k < nreg; ++k) {
+                    h.reg_r[k] = RR(cur, k);
+                    h.reg_v[k] = RV(cur, k);
+                }
+            }
+            load = load_at_cycle_start;
+            status = 2;
+            break;
+        }
+        if (minport != NI_NO_PORT && detect(minport)) break;
+        cur = nb;
+        nreg = nreg_new;
+        if (++t >= tend) break;
+        if (budget && load_before + load > budget) { status = 3; break; }
+    }
+    r.t = t;
+    r.nreg = nreg;
+    r.cur = cur;
+    r.status = status;
+    r.det_cycle = det_cycle;
+    r.det_port = det_port;
+    r.load = load;
+    r.mism = mism;
+}
+
+// Carve a light CTA's dynamic shared memory: [2][KR][B] register values, [KD][B] diff
+// values, [2][KR][B] register ids, [KD][B] diff nets, [KH][B] heap.
+#define LIGHT_CARVE                                                     \
+    extern __shared__ __align__(16) unsigned char lsm[];                \
+    const uint32_t B = blockDim.x, tx = threadIdx.x;                    \
+    uint64_t *rv = reinterpret_cast<uint64_t *>(lsm);                   \
+    uint64_t *dv = rv + 2 * KR * B;                                     \
+    uint32_t *rr = reinterpret_cast<uint32_t *>(dv + KD * B);           \
+    uint32_t *dn = rr + 2 * KR * B;                                     \
+    uint32_t *hp = dn + KD * B;
+
+// Final result of a fault that stopped (detected, over budget, or at the design's last
+// cycle); in no-drop mode a detection was recorded when it happened.
+__device__ __forceinline__ void light_finish(const DevFaults &f, uint32_t fid, const LightRun &r,
+                                             unsigned long long *budget_hit) {
+    if (r.status == 0 && f.mism) return;
+    f.res_det[fid] = r.status == 1 ? 1 : r.status == 3 ? 255 : 0;
+    f.res_cycle[fid] = r.det_cycle;
+    f.res_port[fid] = r.det_port;
+    if (r.status == 3) atomicAdd(budget_hit, 1ull);
+}
+
+template <int KR, int KD, int KH>
+__global__ void __launch_bounds__(256, 1)
+light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
+    LIGHT_CARVE
+    (void)tx;
+    const Promote prom{q.heavy_items, q.heavy_count, q.heavy_cap};
+    for (;;) {
+        const unsigned long long qi = atomicAdd(q.light_head, 1ull);
+        if (qi >= q.n_light) break;
+        const uint32_t fid = q.light_order[qi];
+        const DevDesign &D = designs[f.design[fid]];
+        LightRun r{0, 0, 0, 0, -1, -1, 0, 0};
+        light_run_fault<KR, KD, KH>(D, f, fid, D.T, q.fault_budget, 0, prom, rv, dv, rr, dn, hp, r);
+        f.load[fid] = r.load;
+        if (f.mism) f.mism[fid] += r.mism;
+        if (r.status != 2) light_finish(f, fid, r, q.budget_hit);
+        // t is the first cycle not completed (a detection cycle counts as simulated)
+        atomicAdd(q.counters + 0, (unsigned long long)r.load);
+        atomicAdd(q.counters + 1, (unsigned long long)(r.status == 1 ? r.t + 1 : r.t));
+    }
+}
+
+// Windowed light kernel: the light kernel over cycles [t0, t1) of the live faults;
+// survivors carry their register diffs to the next window.
+template <int KR, int KD, int KH>
+__global__ void __launch_bounds__(256, 1)
+light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight q) {
+    LIGHT_CARVE
+    const Promote prom{q.prom, q.prom_total, q.prom_cap};
     const uint32_t n_live = *q.n_live_in;
     const uint32_t lane = tx & 31u;
     for (;;) {
@@ -1163,212 +1276,25 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
         // take them back to front so the slowest start first (longest processing time first).
         const uint32_t fid = q.live_in[q.reverse ? n_live - 1 - (uint32_t)qi : (uint32_t)qi];
         const DevDesign &D = designs[f.design[fid]];
-        const uint32_t I = D.I, IR = D.I + D.R, T = D.T;
-        const uint32_t tend = min(q.t1, T);     // this window ends at tend
-        const uint64_t *__restrict__ gcol = D.gcol;
-        const uint4 *__restrict__ netinfo = D.netinfo;
-        const uint4 *__restrict__ desc = D.desc;
-        const uint32_t *__restrict__ fo_idx = D.fo_idx;
-        const uint32_t *__restrict__ dreg_off = D.dreg_off;
-        const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
-        const uint32_t site = f.site[fid];
-        const uint32_t bit = f.bit[fid];
-        const bool sv = f.val[fid] != 0;
-        const uint64_t bm = 1ull << bit;
-        const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
-        const uint32_t site_node = site >= IR ? site - IR : 0xFFFFFFFFu;
-
-        uint32_t t = q.t0, nreg = q.st_nreg[fid], cur = 0;
-        for (uint32_t k = 0; k < nreg; ++k) {   // register diffs carried from the last window
+        const uint32_t tend = min(q.t1, D.T);     // this window ends at tend
+        LightRun r{q.t0, q.st_nreg[fid], 0, 0, -1, -1, 0, 0};
+        for (uint32_t k = 0; k < r.nreg; ++k) {   // register diffs carried from the last window
             RR(0, k) = q.st_r[(size_t)k * q.F + fid];
             RV(0, k) = q.st_v[(size_t)k * q.F + fid];
         }
         const uint64_t load_before = f.load[fid];
-        uint64_t load = 0;
-        int status = 0;                 // 1 detected, 2 promoted, 3 budget
-        int32_t det_cycle = -1, det_port = -1;
-
-        for (;;) {
-            if (nreg == 0) {
-                // Skip quiescent cycles: nothing differs unless the site bit is activated.
-                // With the activation bitplane, 64 cycles per load; else four cycles per step.
-                const uint64_t want = sv ? bm : 0ull;   // site bit equal to the stuck value: quiescent
-                if (f.act) {
-                    t = next_active(f.act + (size_t)fid * f.act_stride, t, tend);
-                } else {
-                    while (t + 4 <= tend) {
-                        const uint64_t g0 = __ldg(scol + t), g1 = __ldg(scol + t + 1);
-                        const uint64_t g2 = __ldg(scol + t + 2), g3 = __ldg(scol + t + 3);
-                        if ((g0 & bm) != want) break;
-                        if ((g1 & bm) != want) { t += 1; break; }
-                        if ((g2 & bm) != want) { t += 2; break; }
-                        if ((g3 & bm) != want) { t += 3; break; }
-                        t += 4;
-                    }
-                    if (t + 4 > tend) {
-                        while (t < tend && (__ldg(scol + t) & bm) == want) ++t;
-                    }
-                }
-                if (t >= tend) break;
-            }
-            const uint32_t nb = cur ^ 1u;
-            uint32_t nd = 0, nh = 0, nreg_new = 0, minport = NI_NO_PORT;
-            uint64_t filter = 0;
-            bool ovf = false;
-            const uint64_t load_at_cycle_start = load;   // the heavy kernel redoes a promoted cycle
-
-            auto heap_push = [&](uint32_t x) {
-                if (nh >= (uint32_t)KH) { ovf = true; return; }
-                uint32_t i = nh++;
-                while (i > 0) {
-                    const uint32_t p = (i - 1) >> 1;
-                    const uint32_t hpv = HP(p);
-                    if (hpv <= x) break;
-                    HP(i) = hpv;
-                    i = p;
-                }
-                HP(i) = x;
-            };
-            auto heap_pop = [&]() -> uint32_t {
-                const uint32_t top = HP(0);
-                const uint32_t x = HP(--nh);
-                uint32_t i = 0;
-                for (;;) {
-                    uint32_t c = 2 * i + 1;
-                    if (c >= nh) break;
-                    uint32_t cv = HP(c);
-                    if (c + 1 < nh) {
-                        const uint32_t cv2 = HP(c + 1);
-                        if (cv2 < cv) { cv = cv2; ++c; }
-                    }
-                    if (x <= cv) break;
-                    HP(i) = cv;
-                    i = c;
-                }
-                if (nh > 0) HP(i) = x;
-                return top;
-            };
-            // Keep net (faulty v, good g, record ni): diff entry, detection, fan-out, latch.
-            auto add_diff = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni) {
-                if (nd >= (uint32_t)KD) { ovf = true; return; }
-                DN(nd) = net;
-                DV(nd) = v;
-                ++nd;
-                filter |= 1ull << (net & 63u);
-                const uint32_t p = ni_port(ni.w);
-                minport = p < minport ? p : minport;
-                if (ni.y - ni.x > (uint32_t)KH) { ovf = true; return; }
-                for (uint32_t e = ni.x; e < ni.y; e += 4) {
-                    // four independent loads in flight, then the pushes
-                    const uint32_t c0 = __ldg(fo_idx + e);
-                    const uint32_t c1 = e + 1 < ni.y ? __ldg(fo_idx + e + 1) : 0xFFFFFFFFu;
-                    const uint32_t c2 = e + 2 < ni.y ? __ldg(fo_idx + e + 2) : 0xFFFFFFFFu;
-                    const uint32_t c3 = e + 3 < ni.y ? __ldg(fo_idx + e + 3) : 0xFFFFFFFFu;
-                    heap_push(c0);
-                    if (c1 != 0xFFFFFFFFu) heap_push(c1);
-                    if (c2 != 0xFFFFFFFFu) heap_push(c2);
-                    if (c3 != 0xFFFFFFFFu) heap_push(c3);
-                }
-                uint32_t nr = ni_nreg(ni.w);
-                if (nr) {
-                    if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
-                    for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
-                        const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
-                        const uint32_t r = rec & 0x1FFFFFFu;
-                        const uint64_t wm = wmask(rec >> 25);
-                        const uint64_t qv = v & wm;
-                        if (qv != (g & wm)) {
-                            if (nreg_new >= (uint32_t)KR) { ovf = true; return; }
-                            RR(nb, nreg_new) = r;
-                            RV(nb, nreg_new) = qv;
-                            ++nreg_new;
-                        }
-                    }
-                }
-            };
-            auto lookup = [&](uint32_t x) -> uint64_t {
-                if ((filter >> (x & 63u)) & 1ull) {
-                    for (uint32_t k = 0; k < nd; ++k)
-                        if (DN(k) == x) return DV(k);
-                }
-                return __ldg(gcol + (size_t)x * T + t);
-            };
-
-            bool site_seeded = false;
-            for (uint32_t k = 0; k < nreg && !ovf; ++k) {
-                const uint32_t net = I + RR(cur, k);
-                uint64_t qv = RV(cur, k);
-                if (net == site) { qv = force_bit(qv, bm, sv); site_seeded = true; }
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                if (qv != g) add_diff(net, qv, g, __ldg(netinfo + net));
-            }
-            if (site < IR && !site_seeded && !ovf) {
-                const uint64_t g = __ldg(scol + t);
-                const uint64_t fv = force_bit(g, bm, sv);
-                if (fv != g) add_diff(site, fv, g, __ldg(netinfo + site));
-            }
-            if (site_node != 0xFFFFFFFFu && !ovf) heap_push(site_node);
-            uint32_t last = 0xFFFFFFFFu;
-            while (nh > 0 && !ovf) {
-                const uint32_t n = heap_pop();
-                if (n == last) continue;
-                last = n;
-                const uint32_t net = IR + n;
-                // independent loads first: descriptor, net record, good value
-                const uint4 d = __ldg(desc + n);
-                const uint4 ni = __ldg(netinfo + net);
-                const uint64_t g = __ldg(gcol + (size_t)net * T + t);
-                const uint32_t op = meta_op(d.w);
-                const int no = n_operands(op);
-                uint64_t a = 0, b = 0, c = 0;
-                if (no >= 1) a = lookup(d.x);
-                if (no >= 2) b = lookup(d.y);
-                if (no >= 3) c = lookup(d.z);
-                uint64_t v = eval_op(d, a, b, c);
-                if (n == site_node) v = force_bit(v, bm, sv);
-                ++load;
-                if (v != g) add_diff(net, v, g, ni);
-            }
-            if (ovf) {
-                const uint32_t p = atomicAdd(q.prom_total, 1u);
-                if (p < q.prom_cap) {
-                    HeavyItem &h = q.prom[p];
-                    h.fault = fid;
-                    h.t = t;
-                    h.nreg = nreg;
-                    for (uint32_t k = 0; k < nreg; ++k) {
-                        h.reg_r[k] = RR(cur, k);
-                        h.reg_v[k] = RV(cur, k);
-                    }
-                }
-                load = load_at_cycle_start;
-                status = 2;
-                break;
-            }
-            if (minport != NI_NO_PORT) {
-                det_cycle = (int32_t)t;
-                det_port = (int32_t)minport;
-                status = 1;
-                break;
-            }
-            cur = nb;
-            nreg = nreg_new;
-            if (++t >= tend) break;
-            if (q.fault_budget && load_before + load > q.fault_budget) { status = 3; break; }
-        }
-        f.load[fid] = load_before + load;
-        if (status == 1 || status == 3 || (status == 0 && tend == T)) {
-            f.res_det[fid] = status == 1 ? 1 : status == 3 ? 255 : 0;
-            f.res_cycle[fid] = det_cycle;
-            f.res_port[fid] = det_port;
-            if (status == 3) atomicAdd(q.budget_hit, 1ull);
-        } else if (status == 0) {
+        light_run_fault<KR, KD, KH>(D, f, fid, tend, q.fault_budget, load_before, prom, rv, dv, rr, dn, hp, r);
+        f.load[fid] = load_before + r.load;
+        if (f.mism) f.mism[fid] += r.mism;
+        if (r.status == 1 || r.status == 3 || (r.status == 0 && tend == D.T)) {
+            light_finish(f, fid, r, q.budget_hit);
+        } else if (r.status == 0) {
             // alive at the end of the window: carry the register diffs, append to the
             // survivors (warp-aggregated: one atomic per group of lanes arriving together)
-            q.st_nreg[fid] = (uint8_t)nreg;
-            for (uint32_t k = 0; k < nreg; ++k) {
-                q.st_r[(size_t)k * q.F + fid] = RR(cur, k);
-                q.st_v[(size_t)k * q.F + fid] = RV(cur, k);
+            q.st_nreg[fid] = (uint8_t)r.nreg;
+            for (uint32_t k = 0; k < r.nreg; ++k) {
+                q.st_r[(size_t)k * q.F + fid] = RR(r.cur, k);
+                q.st_v[(size_t)k * q.F + fid] = RV(r.cur, k);
             }
             const unsigned m = __activemask();
             const int leader = __ffs(m) - 1;
@@ -1379,15 +1305,16 @@ light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight
             q.live_out[base + rank] = fid;
         }
         // t is the first cycle not completed (a detection cycle counts as simulated)
-        atomicAdd(q.counters + 0, (unsigned long long)load);
-        atomicAdd(q.counters + 1, (unsigned long long)((status == 1 ? t + 1 : t) - q.t0));
+        atomicAdd(q.counters + 0, (unsigned long long)r.load);
+        atomicAdd(q.counters + 1, (unsigned long long)((r.status == 1 ? r.t + 1 : r.t) - q.t0));
     }
+}
+#undef LIGHT_CARVE
 #undef RV
 #undef RR
 #undef DV
 #undef DN
 #undef HP
-}
 
 // ===================================================================================
 // Plain GPU form: one thread per fault, one flat launch per design (and wave), no
@@ -1412,16 +1339,25 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
     uint32_t *hp = heap_all + (size_t)tid * snode;
     uint32_t *regr = regr_all + (size_t)tid * 2 * sreg;
     uint64_t *regv = regv_all + (size_t)tid * 2 * sreg;
-    const uint32_t site = f.site[fid];
-    const uint32_t bit = f.bit[fid];
-    const bool sv = f.val[fid] != 0;
-    const uint64_t bm = 1ull << bit;
-    uint32_t nreg = 0, cur = 0, epoch = 0;
+    const FaultSite fs = load_fault(f, fid);
+    const uint32_t site = fs.site;
+    const bool nodrop = f.mism != nullptr;
+    uint32_t nreg = 0, cur = 0, epoch = 0, mism = 0;
     uint64_t load = 0;
     int32_t det_cycle = -1, det_port = -1;
-    int status = 0;
     for (uint32_t t = 0; t < T; ++t) {
         ++epoch;
+        if (fs.port != NO_PORT) {
+            // a port fault: the machines differ exactly where the fault changes what the
+            // port observes of the (good) site net
+            const uint64_t g = gcol[(size_t)site * T + t];
+            if (fs.apply(g, t) == g) continue;
+            ++load;
+            if (det_cycle < 0) { det_cycle = (int32_t)t; det_port = (int32_t)fs.port; }
+            ++mism;
+            if (!nodrop) break;
+            continue;
+        }
         const uint32_t nb = cur ^ 1u;
         uint32_t nh = 0, nreg_new = 0, minport = NO_PORT;
         auto push = [&](uint32_t x) {
@@ -1474,16 +1410,16 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
         for (uint32_t k = 0; k < nreg; ++k) {
             const uint32_t net = I + regr[cur * sreg + k];
             uint64_t qv = regv[cur * sreg + k];
-            if (net == site) { qv = force_bit(qv, bm, sv); site_seeded = true; }
+            if (net == site) { qv = fs.apply(qv, t); site_seeded = true; }
             const uint64_t g = gcol[(size_t)net * T + t];
             if (qv != g) keep(net, qv, g);
         }
         if (site < IR && !site_seeded) {
             const uint64_t g = gcol[(size_t)site * T + t];
-            const uint64_t fv = force_bit(g, bm, sv);
+            const uint64_t fv = fs.apply(g, t);
             if (fv != g) keep(site, fv, g);
         }
-        if (site >= IR) push(site - IR);
+        if (site >= IR && fs.acts(t)) push(site - IR);
         while (nh > 0) {
             const uint32_t n = pop();
             const uint4 d = D.desc[n];
@@ -1495,22 +1431,22 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
             if (no >= 3) c = lookup(d.z);
             const uint32_t net = IR + n;
             uint64_t v = eval_op(d, a, b, c);
-            if (net == site) v = force_bit(v, bm, sv);
+            if (net == site) v = fs.apply(v, t);
             ++load;
             const uint64_t g = gcol[(size_t)net * T + t];
             if (v != g) keep(net, v, g);
         }
         if (minport != NO_PORT) {
-            det_cycle = (int32_t)t;
-            det_port = (int32_t)minport;
-            status = 1;
-            break;
+            if (det_cycle < 0) { det_cycle = (int32_t)t; det_port = (int32_t)minport; }
+            ++mism;
+            if (!nodrop) break;
         }
         nreg = nreg_new;
         cur = nb;
     }
     f.load[fid] = load;
-    f.res_det[fid] = status == 1 ? 1 : 0;
+    if (nodrop) f.mism[fid] = mism;
+    f.res_det[fid] = det_cycle >= 0 ? 1 : 0;
     f.res_cycle[fid] = det_cycle;
     f.res_port[fid] = det_port;
 }

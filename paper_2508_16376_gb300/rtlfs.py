@@ -30,8 +30,11 @@ FAULT_DTYPE = np.dtype([("net", np.uint32), ("bit", np.uint8), ("stuck", np.uint
                         ("reserved", np.uint16)])
 RESULT_DTYPE = np.dtype([("cycle", np.int32), ("port", np.int32), ("detected", np.uint8),
                          ("reserved", np.uint8, 3)])
+FAULT_EX_DTYPE = np.dtype([("net", np.uint32), ("bit", np.uint8), ("kind", np.uint8),
+                           ("reserved", np.uint16), ("cycle", np.uint32), ("reserved2", np.uint32)])
+FAULT_SA0, FAULT_SA1, FAULT_SEU, FAULT_SET = 0, 1, 2, 3
 assert NODE_DTYPE.itemsize == 24 and REG_DTYPE.itemsize == 8
-assert FAULT_DTYPE.itemsize == 8 and RESULT_DTYPE.itemsize == 12
+assert FAULT_DTYPE.itemsize == 8 and RESULT_DTYPE.itemsize == 12 and FAULT_EX_DTYPE.itemsize == 16
 
 
 class rtlfs_run_opts(ctypes.Structure):
@@ -39,8 +42,8 @@ class rtlfs_run_opts(ctypes.Structure):
                 ("heavy_block", ctypes.c_int32), ("heavy_ctas", ctypes.c_int32),
                 ("heavy_frac", ctypes.c_float), ("use_graph", ctypes.c_int32),
                 ("fault_budget", ctypes.c_uint64), ("light_cap", ctypes.c_int32),
-                ("window", ctypes.c_int32), ("good_cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("window", ctypes.c_int32), ("no_drop", ctypes.c_int32),
+                ("good_cluster", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 4)]
 
 
 class rtlfs_stats(ctypes.Structure):
@@ -73,6 +76,8 @@ EXPORTS = {
                            ctypes.c_uint32, V], ctypes.c_int),
     "rtlfs_set_stimulus": ([V, ctypes.c_uint32, V, ctypes.c_uint32], ctypes.c_int),
     "rtlfs_set_faults": ([V, ctypes.c_uint32, V, ctypes.c_uint32], ctypes.c_int),
+    "rtlfs_set_faults_ex": ([V, ctypes.c_uint32, V, ctypes.c_uint32], ctypes.c_int),
+    "rtlfs_mismatch_counts": ([V, ctypes.c_uint32, V], ctypes.c_int),
     "rtlfs_run": ([V, V, V, V], ctypes.c_int),
     "rtlfs_run_plain": ([V, V], ctypes.c_int),
     "rtlfs_get_stats": ([V, V], ctypes.c_int),
@@ -185,6 +190,36 @@ def fault_array(faults) -> np.ndarray:
 def rtlfs_set_faults(ctx, design_id: int, faults: np.ndarray) -> None:
     x = np.ascontiguousarray(faults, FAULT_DTYPE)
     _check(ctx, load_library().rtlfs_set_faults(ctx, design_id, _ptr(x), len(x)))
+
+
+def fault_array_ex(faults) -> np.ndarray:
+    a = np.zeros(len(faults), FAULT_EX_DTYPE)
+    a["net"] = faults.net
+    a["bit"] = faults.bit
+    a["kind"] = faults.val
+    if getattr(faults, "cycle", None) is not None:
+        a["cycle"] = faults.cycle
+    return a
+
+
+def rtlfs_set_faults_ex(ctx, design_id: int, faults: np.ndarray) -> None:
+    x = np.ascontiguousarray(faults, FAULT_EX_DTYPE)
+    _check(ctx, load_library().rtlfs_set_faults_ex(ctx, design_id, _ptr(x), len(x)))
+
+
+def rtlfs_mismatch_counts(ctx, design_id: int, n_faults: int) -> np.ndarray:
+    out = np.zeros(max(n_faults, 0), np.uint32)
+    _check(ctx, load_library().rtlfs_mismatch_counts(ctx, design_id, _ptr(out)))
+    return out
+
+
+def _set_any_faults(ctx, did: int, faults) -> None:
+    """Stuck-at lists through rtlfs_set_faults, lists with transient kinds through the
+    extended entry point."""
+    if getattr(faults, "cycle", None) is not None:
+        rtlfs_set_faults_ex(ctx, did, fault_array_ex(faults))
+    else:
+        rtlfs_set_faults(ctx, did, fault_array(faults))
 
 
 def make_opts(**kw) -> rtlfs_run_opts:
@@ -327,15 +362,19 @@ class Simulator:
     def add(self, design, stim: np.ndarray, faults) -> int:
         did = rtlfs_load_design(self.ctx, *design_arrays(design))
         rtlfs_set_stimulus(self.ctx, did, stim)
-        rtlfs_set_faults(self.ctx, did, fault_array(faults))
+        _set_any_faults(self.ctx, did, faults)
         self.designs.append(design)
         self.n_faults.append(len(faults))
         self.T.append(int(stim.shape[0]))
         return did
 
     def set_faults(self, did: int, faults) -> None:
-        rtlfs_set_faults(self.ctx, did, fault_array(faults))
+        _set_any_faults(self.ctx, did, faults)
         self.n_faults[did] = len(faults)
+
+    def mismatch_counts(self, did: int) -> np.ndarray:
+        """Per fault: cycles with a differing output in the last no-drop run."""
+        return rtlfs_mismatch_counts(self.ctx, did, self.n_faults[did])
 
     def run(self, want_load: bool = False, **opts):
         o = make_opts(**opts) if opts else None

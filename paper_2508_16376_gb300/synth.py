@@ -83,22 +83,30 @@ class Design:
 
 @dataclasses.dataclass
 class Faults:
-    """Stuck-at fault descriptors: bit `bit` of net `net` forced to `val` (0 or 1)."""
+    """Fault descriptors: bit `bit` of net `net` (ids n_net + o: output port o). `val` is
+    the kind: 0 / 1 stuck-at 0 / 1, 2 an SEU (register) and 3 an SET (input, node or port)
+    flipping the bit in cycle `cycle` (None: every fault is a stuck-at)."""
     net: np.ndarray   # uint32 [F]
     bit: np.ndarray   # uint8 [F]
     val: np.ndarray   # uint8 [F]
+    cycle: Optional[np.ndarray] = None   # uint32 [F]
 
     def __len__(self) -> int:
         return int(self.net.shape[0])
 
     def take(self, idx) -> "Faults":
-        return Faults(self.net[idx], self.bit[idx], self.val[idx])
+        return Faults(self.net[idx], self.bit[idx], self.val[idx],
+                      None if self.cycle is None else self.cycle[idx])
 
     @staticmethod
     def concat(parts: Sequence["Faults"]) -> "Faults":
+        cyc = None
+        if any(p.cycle is not None for p in parts):
+            cyc = np.concatenate([p.cycle if p.cycle is not None else np.zeros(len(p), np.uint32)
+                                  for p in parts]).astype(np.uint32)
         return Faults(np.concatenate([p.net for p in parts]).astype(np.uint32),
                       np.concatenate([p.bit for p in parts]).astype(np.uint8),
-                      np.concatenate([p.val for p in parts]).astype(np.uint8))
+                      np.concatenate([p.val for p in parts]).astype(np.uint8), cyc)
 
 
 class _Builder:
@@ -437,6 +445,38 @@ def fault_universe(design: Design, include_inputs: bool = False) -> Faults:
     bit2 = np.repeat(bits, 2)
     val2 = np.tile(np.array([0, 1], np.int64), net_rep.shape[0])
     return Faults(net2.astype(np.uint32), bit2.astype(np.uint8), val2.astype(np.uint8))
+
+
+def port_faults(design: Design) -> Faults:
+    """SA0 and SA1 on every bit of every output port (net ids n_net + o: a virtual node
+    between the port's net and the port); ordered by port, bit, stuck value."""
+    widths = design.net_widths().astype(np.int64)
+    w = widths[np.asarray(design.outputs, np.int64)]
+    ports = np.arange(len(w), dtype=np.int64) + design.n_net
+    net_rep = np.repeat(ports, w)
+    starts = np.repeat(np.cumsum(w) - w, w)
+    bits = np.arange(int(w.sum()), dtype=np.int64) - starts
+    return Faults(np.repeat(net_rep, 2).astype(np.uint32), np.repeat(bits, 2).astype(np.uint8),
+                  np.tile(np.array([0, 1], np.int64), net_rep.shape[0]).astype(np.uint8))
+
+
+def transient_faults(design: Design, F: int, T: int, seed: int, port_share: float = 0.05) -> Faults:
+    """F transient faults: SEUs on register bits (kind 2) and SETs on input, node and
+    output-port bits (kind 3), each at a cycle uniform in [0, T]; cycle T never acts."""
+    rng = np.random.default_rng(seed)
+    widths = design.net_widths().astype(np.int64)
+    n_port = int(round(F * port_share)) if design.n_out else 0
+    nets = rng.integers(0, design.n_net, F - n_port)
+    ports = rng.integers(0, max(design.n_out, 1), n_port) if n_port else np.zeros(0, np.int64)
+    out_w = widths[np.asarray(design.outputs, np.int64)] if design.n_out else np.zeros(0, np.int64)
+    net = np.concatenate([nets, ports + design.n_net]).astype(np.int64)
+    w = np.concatenate([widths[nets], out_w[ports] if n_port else np.zeros(0, np.int64)])
+    bit = (rng.random(F) * w).astype(np.int64)
+    is_reg = (net >= design.n_in) & (net < design.n_in + design.n_reg)
+    kind = np.where(is_reg, 2, 3)
+    cycle = rng.integers(0, T + 1, F)
+    return Faults(net.astype(np.uint32), bit.astype(np.uint8), kind.astype(np.uint8),
+                  cycle.astype(np.uint32))
 
 
 def sample_faults(design: Design, F: int, seed: int) -> Faults:

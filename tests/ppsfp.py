@@ -56,7 +56,10 @@ def evaluate(design, fault: Optional[Tuple[int, int, int]] = None) -> Tuple[List
     def force(net_id: int, bits: List[int]) -> List[int]:
         if fault is not None and fault[0] == net_id:
             bits = list(bits)
-            bits[fault[1]] = ALL if fault[2] else 0
+            if fault[2] >= 2:              # a flip in every vector (transient model)
+                bits[fault[1]] ^= ALL
+            else:
+                bits[fault[1]] = ALL if fault[2] else 0
         return bits
 
     j = 0
@@ -165,3 +168,52 @@ def exhaustive_stimulus(design) -> np.ndarray:
         cols.append((p >> np.uint64(j)) & np.uint64((1 << w) - 1))
         j += w
     return np.ascontiguousarray(np.stack(cols, axis=1).astype(np.uint64))
+
+
+def brute_force_ex(design, faults) -> Tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+    """(detected, first vector, first port, vectors with a differing port) under the
+    exhaustive stimulus, for the general fault list: kinds 0/1 stuck-at, kind 3 (SET) a
+    flip in the single vector faults.cycle[f]; net ids n_net + o are output-port faults,
+    whose force applies to what port o observes only. For a combinational design the
+    machines of different vectors are independent, so an SET at vector c is detected iff
+    the flip, applied to every vector at once, changes an output in vector c."""
+    good, bs = evaluate(design)
+    F = len(faults)
+    det = np.zeros(F, np.uint8)
+    cyc = np.full(F, -1, np.int32)
+    port = np.full(F, -1, np.int32)
+    count = np.zeros(F, np.uint32)
+    outs = [int(o) for o in design.outputs]
+    n_net = design.n_net
+    for f in range(F):
+        net, b, kind = int(faults.net[f]), int(faults.bit[f]), int(faults.val[f])
+        per_port = []
+        if net >= n_net:        # port fault: the other ports see the good machine
+            o = net - n_net
+            for q, on in enumerate(outs):
+                d = 0
+                if q == o:
+                    g = good[on][b]
+                    d = g ^ (bs.ALL ^ g if kind >= 2 else (bs.ALL if kind else 0))
+                per_port.append(d)
+        else:
+            bad, _ = evaluate(design, (net, b, kind))
+            for on in outs:
+                d = 0
+                for x, y in zip(good[on], bad[on]):
+                    d |= x ^ y
+                per_port.append(d)
+        anydiff = 0
+        for d in per_port:
+            anydiff |= d
+        if kind >= 2:           # only the flip's own vector can differ
+            c = int(faults.cycle[f])
+            anydiff &= (1 << c) if c < bs.P else 0
+            per_port = [d & anydiff for d in per_port]
+        count[f] = bin(anydiff).count("1")
+        if anydiff:
+            p0 = (anydiff & -anydiff).bit_length() - 1
+            det[f] = 1
+            cyc[f] = p0
+            port[f] = next(i for i, d in enumerate(per_port) if (d >> p0) & 1)
+    return det, cyc, port, count

@@ -39,8 +39,53 @@ def test_struct_sizes_match_header():
     assert rtlfs.REG_DTYPE.itemsize == 8
     assert rtlfs.FAULT_DTYPE.itemsize == 8
     assert rtlfs.RESULT_DTYPE.itemsize == 12
+    assert rtlfs.FAULT_EX_DTYPE.itemsize == 16
     assert ctypes.sizeof(rtlfs.rtlfs_run_opts) == 4 * 6 + 8 + 32
     assert ctypes.sizeof(rtlfs.rtlfs_stats) == 6 * 8 + 4 * 8 + 8 + 4 * 8
+
+
+def test_binding_layouts_match_the_compiled_header(tmp_path):
+    """Sizes and field offsets as a C compiler lays out include/rtlfs.h equal the
+    binding's ctypes structures and numpy record types."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    checks = {
+        "rtlfs_node": ("NODE_DTYPE", ["op", "width", "a", "b", "c", "imm"]),
+        "rtlfs_reg": ("REG_DTYPE", ["d_net", "width"]),
+        "rtlfs_fault": ("FAULT_DTYPE", ["net", "bit", "stuck"]),
+        "rtlfs_fault_ex": ("FAULT_EX_DTYPE", ["net", "bit", "kind", "cycle"]),
+        "rtlfs_result": ("RESULT_DTYPE", ["cycle", "port", "detected"]),
+    }
+    ctypes_checks = {"rtlfs_run_opts": rtlfs.rtlfs_run_opts, "rtlfs_stats": rtlfs.rtlfs_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rtlfs.h"', "int main(void) {"]
+    for st, (_, fields) in checks.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for fl in fields:
+            lines.append(f'printf("{st} {fl} %zu\\n", offsetof({st}, {fl}));')
+    for st, cls in ctypes_checks.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for fl, _ in cls._fields_:
+            if fl != "reserved":
+                lines.append(f'printf("{st} {fl} %zu\\n", offsetof({st}, {fl}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = str(tmp_path / "layout")
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(root, "include"), "-o", exe, str(src)])
+    got = {}
+    for line in subprocess.check_output([exe]).decode().splitlines():
+        st, fl, v = line.split()
+        got[(st, fl)] = int(v)
+    for st, (dt, fields) in checks.items():
+        d = getattr(rtlfs, dt)
+        assert got[(st, "size")] == d.itemsize, st
+        for fl in fields:
+            assert got[(st, fl)] == d.fields[fl][1], (st, fl)
+    for st, cls in ctypes_checks.items():
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for fl, _ in cls._fields_:
+            if fl != "reserved":
+                assert got[(st, fl)] == getattr(cls, fl).offset, (st, fl)
 
 
 def test_create_without_device_fails_cleanly():

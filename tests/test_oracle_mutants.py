@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import ppsfp
+import test_oracle_fault_models as fm
 import test_oracle_pins as pins
 from paper_2508_16376_gb300 import synth
 
@@ -34,8 +35,11 @@ MUTANTS = {
                            "Q[r] = net[d->reg_d[r]];"),
     "stuck_value_inverted": ("if (fault_val) m1 = (uint64_t)1 << fault_bit;",
                              "if (!fault_val) m1 = (uint64_t)1 << fault_bit;"),
-    "highest_port_wins": ("for (int32_t o = 0; o < O; o++) {\n                if (net[d->out[o]]",
-                          "for (int32_t o = O - 1; o >= 0; o--) {\n                if (net[d->out[o]]"),
+    "highest_port_wins": ("for (int32_t o = 0; o < O; o++) {\n                uint64_t seen",
+                          "for (int32_t o = O - 1; o >= 0; o--) {\n                uint64_t seen"),
+    "flip_in_every_cycle": ("fx = (int64_t)t == fault_cycle ? mx : 0;", "fx = mx;"),
+    "nodrop_counts_once": ("++*mism;", "*mism = 1;"),
+    "port_fault_ignored": ("if ((int64_t)o == fault_port) seen = FAULTY(seen);", ""),
 }
 
 
@@ -50,6 +54,9 @@ def _pins_pass() -> bool:
         pins.test_brute_force_covers_every_op()
         pins.test_register_truncates_wider_d()
         _multi_port_pin()
+        fm.test_counter4_extended_golden()
+        fm.test_delay_chain_transient_closed_form(4, 5, 30)
+        fm.test_brute_force_fault_models(0)
     except AssertionError:
         return False
     return True
