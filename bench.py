@@ -47,10 +47,14 @@ def _dist():
     return ws, rank, local
 
 
-def workload(rank: int):
+def workload(rank: int, cycles: int = 0):
+    """The medium workload; `cycles` > 0 keeps only the first that many stimulus cycles
+    (a short case of the same design and faults, for profiler captures)."""
     from paper_2508_16376_gb300 import synth
     d = synth.medium_design(WORKLOAD["design_seed"])
     stim = synth.stimulus(d, WORKLOAD["cycles"], WORKLOAD["stim_seed"], WORKLOAD["hold_frac"])
+    if cycles:
+        stim = stim[:cycles]
     faults = synth.sample_faults(d, WORKLOAD["faults"], WORKLOAD["fault_seed"] + rank)
     return d, stim, faults
 
@@ -127,7 +131,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    d, stim, faults = workload(0)
+    d, stim, faults = workload(0, args.cycles)
     g = oracle.good_outputs(d, stim)
     cores = os.cpu_count() or 1
     per_step = max(cores, 16)
@@ -165,6 +169,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--opts", default=json.dumps(DEFAULT_OPTS),
                     help="rtlfs_run options as JSON (default: the tuned campaign options)")
+    ap.add_argument("--cycles", type=int, default=0,
+                    help="run only the first N stimulus cycles (a short case for profiling; "
+                         "the JSON line names it in config)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -180,7 +187,7 @@ def main():
     from paper_2508_16376_gb300 import rtlfs
     from paper_2508_16376_gb300.rtlfs import Simulator
     _b.build()
-    d, stim, faults = workload(rank)
+    d, stim, faults = workload(rank, args.cycles)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -243,7 +250,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": dict(WORKLOAD, l2="good trace 2 x 1.77 GB rewritten every step (> L2)",
+            "config": dict(WORKLOAD, cycles=int(stim.shape[0]),
+                           l2="good trace 2 x 8 B x nets x cycles rewritten every step (> L2 at full size)",
                            parallelism=f"fault shards x{ws}", run_opts=run_opts),
             "wall_ms_per_step": 1000 * wall / args.steps,
             "campaign": {k: last[k] for k in ("good_ms", "prep_ms", "light_ms", "heavy_ms",
@@ -263,7 +271,10 @@ def main():
                                   "unit": UNIT, "ms_per_step": pst["total_ms"],
                                   "wall_s": time.perf_counter() - t1}
     from paper_2508_16376_gb300 import roofline
-    line["roofline"] = roofline.dominant_roofline(last, peaks, d, stim.shape[0])
+    window = int(run_opts.get("window", 0))
+    n_win = -(-int(stim.shape[0]) // window) if window else 1
+    line["roofline"] = roofline.dominant_roofline(last, peaks, d, stim.shape[0], launches=n_win,
+                                                  traffic=roofline.measured_traffic(window))
     sim.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(d, stim, faults)

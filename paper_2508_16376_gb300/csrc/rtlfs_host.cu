@@ -1311,6 +1311,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                               ctx->d_wb.p, ctx->d_static_ptrs.p, ctx->w_st_nreg.p, ctx->w_st_r.p,
                               ctx->w_st_v.p, ctx->w_live0.p, ctx->w_live1.p, ctx->w_cnt32.p, ctx->w_cnt64.p,
                               ctx->w_carry0.p, ctx->w_carry1.p, ctx->w_pool_r0.p, ctx->w_pool_r1.p,
+                              ctx->d_fport.p, ctx->d_ft0.p, ctx->d_mism.p,
                               ctx->w_pool_v0.p, ctx->w_pool_v1.p, ctx->d_act.p};
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;

@@ -328,7 +328,8 @@ def test_windowed_matches_oracle(window):
     stim = synth.stimulus(d, 257, 27, 0.1)
     u = synth.sample_faults(d, 3000, 27)
     exp = oracle.fault_sim(d, stim, u, threads=16)
-    for kw in (dict(), dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN, light_cap=1)):
+    for kw in (dict(), dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN, light_cap=1),
+               dict(heavy_frac=1.0)):
         got = gpu_run(d, stim, u, want_load=True, window=window, **kw)
         assert_same(got, exp, f"window {window} {kw}")
     ref = gpu_run(d, stim, u, want_load=True)
