@@ -36,8 +36,10 @@ WORKLOAD = dict(workload="medium datapath+FSM RTL design, stuck-at campaign",
 
 
 # Campaign options the bench times: windows of 256 cycles (good trace, light and heavy
-# kernels overlapped on three streams), default light capacity, one warp per heavy fault.
-DEFAULT_OPTS = {"window": 256}
+# kernels overlapped on three streams), the small light-lane capacity (4 register diffs,
+# 12 net diffs, 12 pending nodes: more faults go to the heavy kernel, whose one-warp form
+# handles them cheaply), one warp per heavy fault.
+DEFAULT_OPTS = {"window": 256, "light_cap": 1}
 
 
 def _dist():

@@ -18,6 +18,7 @@
 // the cycle loop of each fault (no separate synchronization phase, Sec. IV-D).
 #include "rtlfs_internal.h"
 
+#include <climits>
 #include <cstdio>
 
 namespace rtlfs {
@@ -820,7 +821,305 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
     r.mism = mism;
 }
 
-__global__ void __launch_bounds__(1024)
+// One warp per fault (heavy_block = 32): the loop of heavy_run_fault with warp
+// synchronisation in place of block barriers, the level's dirty nodes gathered by a warp
+// prefix sum instead of shared atomics, the detecting port and the evaluation count kept
+// per lane and reduced once per cycle, and the level bitmap cleared once per cycle. Same
+// results and the same evaluation counts as heavy_run_fault.
+__device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const DevFaults &f, uint32_t fid,
+                                                     uint32_t tend, unsigned long long budget,
+                                                     const HeavySmem &sm, HeavyVars &V, uint64_t *fval,
+                                                     uint32_t *regR, uint64_t *regV, uint32_t max_reg,
+                                                     HeavyRun &r) {
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t I = D.I, IR = D.I + D.R, T = D.T, NL = D.n_levels;
+    const uint64_t *__restrict__ gcol = D.gcol;
+    const uint4 *__restrict__ netinfo = D.netinfo;
+    const uint32_t *__restrict__ fo_idx = D.fo_idx;
+    const uint16_t *__restrict__ fo_lvl = D.fo_lvl;
+    const uint32_t *__restrict__ dreg_off = D.dreg_off;
+    const uint32_t *__restrict__ dreg_rec = D.dreg_rec;
+    const FaultSite fs = load_fault(f, fid);
+    const uint32_t site = fs.site;
+    const uint32_t bit = f.bit[fid];
+    const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
+    uint32_t *const bm = sm.bm, *const cnt = sm.cnt, *const dbm = sm.dbm;
+    unsigned long long *const lvm = sm.lvm;
+    const uint32_t nlw = sm.nlw;
+    const bool nodrop = f.mism != nullptr;
+    bool seen = nodrop && f.res_det[fid] == 1;   // no-drop: first detection already recorded
+    // evaluations this run may do before the fault's budget is exceeded (negative when it
+    // already is; unlimited without a budget)
+    const long long room = budget ? (long long)budget - (long long)f.load[fid] : LLONG_MAX;
+    unsigned long long load = 0;                 // this run's evaluations (warp-uniform)
+    uint32_t t = r.t, nreg = r.nreg, cur = 0, mism = 0;
+    int status = 0;
+    int32_t det_cycle = -1, det_port = -1;
+    auto detect = [&](uint32_t port) -> bool {
+        if (!nodrop) {
+            det_cycle = (int32_t)t;
+            det_port = (int32_t)port;
+            status = 1;
+            return true;
+        }
+        if (!seen && lane == 0) {
+            f.res_det[fid] = 1;
+            f.res_cycle[fid] = (int32_t)t;
+            f.res_port[fid] = (int32_t)port;
+        }
+        seen = true;
+        ++mism;
+        return false;
+    };
+    auto mark = [&](uint32_t c, uint32_t lv) {
+        const uint32_t b1 = 1u << (c & 31u);
+        const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
+        if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
+    };
+    auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
+        for (uint32_t e = e0 + first; e < e1; e += step) mark(__ldg(fo_idx + e), __ldg(fo_lvl + e));
+    };
+    uint32_t fr_begin = 0;
+    auto expand = [&]() {   // call after a warp sync
+        const uint32_t end = V.nfr;
+        const uint32_t n = min(end - fr_begin, HEAVY_FRANGE);
+        for (uint32_t k = 0; k < n; ++k) {
+            const uint2 fr = sm.frange[(fr_begin + k) % HEAVY_FRANGE];
+            mark_range(fr.x, fr.y, lane, 32u);
+        }
+        fr_begin = end;
+    };
+    uint32_t pmin = NI_NO_PORT;   // this lane's lowest differing port in the cycle
+    auto keep_value = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni, uint32_t nb) {
+        fval[net] = v;
+        const uint32_t wbit = 1u << (net & 31u);
+        if (!atomicOr(&dbm[net >> 5], wbit)) {
+            const uint32_t k = atomicAdd(&V.nd, 1u);
+            if (k < HEAVY_DLIST) sm.dlist[k] = net >> 5;
+        }
+        pmin = min(pmin, ni_port(ni.w));
+        uint32_t nr = ni_nreg(ni.w);
+        if (nr == 255u) nr = __ldg(dreg_off + net + 1) - ni.z;
+        for (uint32_t e = ni.z; e < ni.z + nr; ++e) {
+            const uint32_t rec = __ldg(dreg_rec + e);   // register | width << 25
+            const uint64_t wm = wmask(rec >> 25);
+            const uint64_t qv = v & wm;
+            if (qv != (g & wm)) {
+                const uint32_t k = atomicAdd(&V.nreg_new, 1u);
+                regR[nb * max_reg + k] = rec & 0x1FFFFFFu;
+                regV[nb * max_reg + k] = qv;
+            }
+        }
+    };
+    auto keep_fanout = [&](uint4 ni) {
+        if (ni.y - ni.x > HEAVY_INLINE_FANOUT) {
+            const uint32_t k = atomicAdd(&V.nfr, 1u);
+            if (k - fr_begin < HEAVY_FRANGE) sm.frange[k % HEAVY_FRANGE] = make_uint2(ni.x, ni.y);
+            else mark_range(ni.x, ni.y, 0, 1);
+        } else {
+            mark_range(ni.x, ni.y, 0, 1);
+        }
+    };
+    auto lookup = [&](uint32_t x) -> uint64_t {
+        if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
+        return __ldg(gcol + (size_t)x * T + t);
+    };
+
+    for (;;) {
+        if (nreg == 0) {   // nothing latched: jump to the next cycle the fault acts by itself
+            if (fs.kind == FK_FLIP) {
+                t = t <= fs.t0 ? min(fs.t0, tend) : tend;
+            } else if (f.act) {
+                const uint32_t tn = lane == 0 ? next_active(f.act + (size_t)fid * f.act_stride, t, tend) : 0u;
+                t = __shfl_sync(FULL, tn, 0);
+            } else {
+                uint32_t found = tend;
+                for (uint32_t tt = t; tt < tend; tt += 32) {
+                    const uint32_t u = tt + lane;
+                    const bool act = u < tend && ((__ldg(scol + u) >> bit) & 1ull) != (uint64_t)fs.kind;
+                    const uint32_t bal = __ballot_sync(FULL, act);
+                    if (bal) { found = tt + __ffs(bal) - 1; break; }
+                }
+                t = found;
+            }
+            if (t >= tend) break;
+            if (fs.port != NO_PORT) {
+                // a port fault changes only what its port observes of the site net
+                ++load;
+                if (detect(fs.port)) break;
+                if (++t >= tend) break;
+                if ((long long)load > room) { status = 3; break; }
+                continue;
+            }
+        }
+        const uint32_t nb = cur ^ 1u;
+        if (lane == 0) { V.nreg_new = 0; V.nd = 0; V.nfr = 0; }
+        fr_begin = 0;
+        pmin = NI_NO_PORT;
+        __syncwarp();
+
+        // registers that carry a difference into this cycle
+        bool seeded = false;
+        for (uint32_t k = lane; k < nreg; k += 32) {
+            const uint32_t net = I + regR[cur * max_reg + k];
+            uint64_t qv = regV[cur * max_reg + k];
+            const uint4 ni = __ldg(netinfo + net);
+            const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+            if (net == site) { qv = fs.apply(qv, t); seeded = true; }
+            if (qv != g) { keep_value(net, qv, g, ni, nb); keep_fanout(ni); }
+        }
+        const bool site_seeded = __any_sync(FULL, seeded);
+        if (lane == 0) {
+            if (site < IR && !site_seeded) {   // input or register site
+                const uint64_t g = __ldg(scol + t);
+                const uint64_t fv = fs.apply(g, t);
+                if (fv != g) {
+                    const uint4 ni = __ldg(netinfo + site);
+                    keep_value(site, fv, g, ni, nb);
+                    keep_fanout(ni);
+                }
+            }
+            if (site >= IR && fs.acts(t)) mark(site - IR, __ldg(D.node_level + site - IR));   // node site
+        }
+        __syncwarp();
+        expand();
+        __syncwarp();
+
+        uint32_t my_load = 0;
+        auto eval_node = [&](uint32_t n) {
+            const uint32_t net = IR + n;
+            const uint4 d = __ldg(D.desc + n);
+            const uint4 ni = __ldg(netinfo + net);
+            const uint64_t g = __ldg(gcol + (size_t)net * T + t);
+            const uint32_t nf = ni.y - ni.x;
+            uint32_t pc[HEAVY_PREFETCH], pl[HEAVY_PREFETCH];
+#pragma unroll
+            for (uint32_t k = 0; k < HEAVY_PREFETCH; ++k) {
+                pc[k] = 0;
+                pl[k] = 0;
+                if (nf <= HEAVY_PREFETCH && k < nf) {
+                    pc[k] = ld_early_u32(fo_idx + ni.x + k);
+                    pl[k] = ld_early_u16(fo_lvl + ni.x + k);
+                }
+            }
+            const uint32_t op = meta_op(d.w);
+            const int no = n_operands(op);
+            uint64_t a = 0, b = 0, c = 0;
+            if (no >= 1) a = lookup(d.x);
+            if (no >= 2) b = lookup(d.y);
+            if (no >= 3) c = lookup(d.z);
+            uint64_t v = eval_op(d, a, b, c);
+            if (net == site) v = fs.apply(v, t);
+            ++my_load;
+            if (v != g) {
+                keep_value(net, v, g, ni, nb);
+                if (nf <= HEAVY_PREFETCH) {
+#pragma unroll
+                    for (uint32_t k = 0; k < HEAVY_PREFETCH; ++k)
+                        if (k < nf) mark(pc[k], pl[k]);
+                } else {
+                    keep_fanout(ni);
+                }
+            }
+        };
+
+        for (uint32_t L = 0;;) {
+            // next level with dirty nodes: bits at or below a processed level are ignored
+            // (marks only go to higher levels) and the whole bitmap is cleared per cycle
+            uint32_t lw = L >> 6;
+            unsigned long long m = lw < nlw ? lvm[lw] & (~0ull << (L & 63u)) : 0ull;
+            while (!m && ++lw < nlw) m = lvm[lw];
+            if (!m) break;
+            L = (lw << 6) + (uint32_t)(__ffsll((long long)m) - 1);
+            if (L >= NL) break;
+            const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
+            const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
+            if (cnt[L] <= HEAVY_NLIST) {
+                // gather: one bitmap word per lane, positions from a warp prefix sum; no
+                // marks happen meanwhile, so each lane clears its word's level bits plainly
+                uint32_t base = 0;
+                for (uint32_t wb = w0; wb <= w1; wb += 32) {
+                    const uint32_t w = wb + lane;
+                    uint32_t bits = 0;
+                    if (w <= w1) {
+                        uint32_t wm = 0xFFFFFFFFu;
+                        if (w == w0) wm &= 0xFFFFFFFFu << (lo & 31u);
+                        if (w == w1 && (hi & 31u)) wm &= (1u << (hi & 31u)) - 1u;
+                        const uint32_t word = bm[w];
+                        bits = word & wm;
+                        if (bits) bm[w] = word & ~wm;
+                    }
+                    const uint32_t cb = (uint32_t)__popc(bits);
+                    uint32_t incl = cb;
+#pragma unroll
+                    for (uint32_t o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    uint32_t k = base + incl - cb;
+                    for (; bits; bits &= bits - 1, ++k)
+                        if (k < HEAVY_NLIST) sm.nlist[k] = (w << 5) + (uint32_t)(__ffs(bits) - 1);
+                    base += __shfl_sync(FULL, incl, 31);
+                }
+                __syncwarp();
+                const uint32_t nl = min(base, HEAVY_NLIST);
+                for (uint32_t i = lane; i < nl; i += 32) eval_node(sm.nlist[i]);
+            } else {
+                for (uint32_t w = w0 + lane; w <= w1; w += 32) {
+                    uint32_t wm = 0xFFFFFFFFu;
+                    if (w == w0) wm &= 0xFFFFFFFFu << (lo & 31u);
+                    if (w == w1 && (hi & 31u)) wm &= (1u << (hi & 31u)) - 1u;
+                    if (!(bm[w] & wm)) continue;
+                    uint32_t bits = atomicAnd(&bm[w], ~wm) & wm;
+                    for (; bits; bits &= bits - 1) eval_node((w << 5) + (uint32_t)(__ffs(bits) - 1));
+                }
+            }
+            __syncwarp();
+            if (V.nfr != fr_begin) {   // uniform: read after the sync
+                expand();
+                __syncwarp();
+            }
+            if (lane == 0) cnt[L] = 0;
+            ++L;
+        }
+        load += __reduce_add_sync(FULL, my_load);
+        const uint32_t minport = __reduce_min_sync(FULL, pmin);
+        __syncwarp();
+        for (uint32_t i = lane; i < nlw; i += 32) lvm[i] = 0;
+        // clear the net bitmap for the next cycle
+        const uint32_t nd = V.nd;
+        if (nd <= HEAVY_DLIST) {
+            for (uint32_t k = lane; k < nd; k += 32) dbm[sm.dlist[k]] = 0;
+        } else {
+            for (uint32_t i = lane; i < sm.nwd; i += 32) dbm[i] = 0;
+        }
+        if (minport != NI_NO_PORT && detect(minport)) break;
+        nreg = V.nreg_new;
+        cur = nb;
+        if (++t >= tend) break;
+        if ((long long)load > room) { status = 3; break; }
+        __syncwarp();
+    }
+    __syncwarp();
+    if (lane == 0) V.load = load;
+    r.t = t;
+    r.nreg = nreg;
+    r.cur = cur;
+    r.status = status;
+    r.det_cycle = det_cycle;
+    r.det_port = det_port;
+    r.mism = mism;
+}
+
+// Barrier of a heavy CTA: one warp (heavy_block = 32) or several.
+template <bool WARP>
+__device__ __forceinline__ void hsync() {
+    if (WARP) __syncwarp(); else __syncthreads();
+}
+
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
@@ -832,14 +1131,14 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
     heavy_zero(sm, S, V);
-    __syncthreads();
+    hsync<WARP>();
 
     for (;;) {
         if (tid == 0) {
             s_item = atomicAdd(q.heavy_head, 1ull);
             s_n_items = min(*((volatile uint32_t *)q.heavy_count), q.heavy_cap);
         }
-        __syncthreads();
+        hsync<WARP>();
         const unsigned long long idx = s_item;
         if (idx >= s_n_items) break;
         const HeavyItem &it = q.heavy_items[idx];
@@ -850,10 +1149,11 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
             regV[k] = it.reg_v[k];
         }
         if (tid == 0) V.load = 0;
-        __syncthreads();
+        hsync<WARP>();
         HeavyRun r{it.t, it.nreg, 0, 0, -1, -1, 0};
-        heavy_run_fault(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
-        __syncthreads();
+        if (WARP) heavy_run_fault_warp(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        else heavy_run_fault(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        hsync<WARP>();
         if (tid == 0) {
             f.load[fid] += V.load;
             if (f.mism) f.mism[fid] += r.mism;
@@ -867,14 +1167,15 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
             const uint32_t t_end = r.status == 1 ? r.t + 1 : min(r.t, D.T);
             atomicAdd(q.counters + 1, (unsigned long long)(t_end - it.t));
         }
-        __syncthreads();
+        hsync<WARP>();
     }
 }
 
 // Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
 // from the last window and those promoted in this one; survivors carry their register
 // diffs to the next window through the pool.
-__global__ void __launch_bounds__(1024)
+template <bool WARP>
+__global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
@@ -885,14 +1186,14 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
     heavy_zero(sm, S, V);
-    __syncthreads();
+    hsync<WARP>();
 
     // written before this launch by earlier work on the stream: the same in every thread
     const uint32_t n_carry = *q.n_carry_in, pb = *q.prom_begin, pe = *q.prom_end;
     const unsigned long long n_items = (unsigned long long)n_carry + (pe - pb);
     for (;;) {
         if (tid == 0) s_item = atomicAdd(q.head, 1ull);
-        __syncthreads();
+        hsync<WARP>();
         const unsigned long long idx = s_item;
         if (idx >= n_items) break;
         const bool carried = idx < n_carry;
@@ -909,10 +1210,11 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
             regV[k] = carried ? q.pool_v_in[cin.off + k] : it.reg_v[k];
         }
         if (tid == 0) V.load = 0;
-        __syncthreads();
+        hsync<WARP>();
         HeavyRun r{t_start, nreg0, 0, 0, -1, -1, 0};
-        heavy_run_fault(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
-        __syncthreads();
+        if (WARP) heavy_run_fault_warp(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        else heavy_run_fault(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        hsync<WARP>();
         const bool carry = r.status == 0 && tend < D.T;   // alive at the end of the window
         if (carry) {
             if (tid == 0) {
@@ -920,7 +1222,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
                 s_off = off + r.nreg <= q.pool_cap ? off : ~0ull;
                 if (s_off == ~0ull) atomicOr(q.err, 2u);
             }
-            __syncthreads();
+            hsync<WARP>();
             const unsigned long long off = s_off;
             if (off != ~0ull) {
                 for (uint32_t k = tid; k < r.nreg; k += B) {
@@ -943,7 +1245,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
             const uint32_t t_end = r.status == 1 ? r.t + 1 : min(r.t, tend);
             atomicAdd(q.counters + 1, (unsigned long long)(t_end - t_start));
         }
-        __syncthreads();
+        hsync<WARP>();
     }
 }
 
@@ -1622,29 +1924,30 @@ size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net
 
 int heavy_max_blocks_per_sm(int block, size_t smem) {
     int n = 0;
-    cudaFuncSetAttribute(heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, heavy_kernel, block, smem);
+    const void *fn = block == 32 ? (const void *)heavy_window_kernel<true> : (const void *)heavy_window_kernel<false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem);
     return n;
 }
 
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream) {
     const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net);
-    cudaError_t e = cudaFuncSetAttribute(heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const void *fn = block == 32 ? (const void *)heavy_kernel<true> : (const void *)heavy_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    heavy_kernel<<<grid, block, smem, stream>>>(d_designs, f, q, s);
-    return cudaGetLastError();
+    void *args[] = {(void *)&d_designs, (void *)&f, (void *)&q, (void *)&s};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
 cudaError_t launch_heavy_window(const DevDesign *d_designs, DevFaults f, WinHeavy w, HeavyScratch s,
                                 int block, int grid, cudaStream_t stream) {
     const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net);
-    cudaError_t e = cudaFuncSetAttribute(heavy_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const void *fn = block == 32 ? (const void *)heavy_window_kernel<true> : (const void *)heavy_window_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    heavy_window_kernel<<<grid, block, smem, stream>>>(d_designs, f, w, s);
-    return cudaGetLastError();
+    void *args[] = {(void *)&d_designs, (void *)&f, (void *)&w, (void *)&s};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
 cudaError_t launch_plain(const DevDesign *d_designs, uint32_t design, DevFaults f, uint32_t first,
