@@ -152,13 +152,18 @@ typedef struct {
                                 paper's evaluation protocol, Sec. V-A): the result keeps the
                                 first detection and rtlfs_mismatch_counts gives each fault's
                                 number of cycles with a differing output */
+    int32_t  heavy_form;     /* heavy kernel's record of differing nets: 0 = auto (the
+                                exact one unless it costs resident CTAs), 1 = a shared-memory
+                                bit per net, 2 = a small shared filter plus cycle stamps on
+                                the values in global scratch (for designs whose per-net
+                                bitmap would crowd shared memory) */
     int32_t  good_cluster;   /* good-trace form: 0 = auto (one CTA with the net values in
                                 shared memory when the design fits, else the smallest
                                 thread-block cluster whose CTAs hold them in distributed
                                 shared memory, else one CTA over the global trace);
                                 1 = one CTA; 2, 4, 8 or 16 = clusters of that many CTAs
                                 (RTLFS_E_ARG when a design cannot run that way) */
-    uint32_t reserved[4];
+    uint32_t reserved[3];
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */

@@ -149,10 +149,14 @@ struct rtlfs_ctx {
     DBuf<uint32_t> d_err;             // set by a kernel whose bounded wait ran out
     DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget,
                                       // [4..5] light evals/cycles, [6..7] heavy evals/cycles
-    DBuf<uint64_t> h_fval;
+    DBuf<HeavyVal> h_fval;
+    DBuf<uint32_t> h_stamp;
     DBuf<uint32_t> h_regr;
     DBuf<uint64_t> h_regv;
     uint32_t heavy_slots = 0, heavy_grid = 0, hs_net = 0, hs_reg = 0, hs_node = 0, hs_lv = 0;
+    bool heavy_exact = false;          // the heavy kernel's form for the current designs
+    bool stamps_stale = false;         // the exact form wrote values over stamp fields since
+                                       // the scratch was last zeroed
     // scheduler state
     DBuf<const float *> d_static_ptrs;
     DBuf<float> d_X, d_heur, d_pred, d_mm;
@@ -734,36 +738,55 @@ DevFaults dev_faults(rtlfs_ctx *ctx) {
     return f;
 }
 
-int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots) {
+int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots, int form) {
     uint32_t mn = 1, mr = 1, mnode = 1, ml = 1;
     for (Design *D : ctx->designs) {
         mn = std::max(mn, D->n_net); mr = std::max(mr, D->R);
         mnode = std::max(mnode, D->N); ml = std::max(ml, D->n_levels);
     }
-    const size_t smem = heavy_smem_bytes(mnode, ml, mn);
-    if (smem > 220 * 1024) return fail(ctx, RTLFS_E_ARG, "design too large for the heavy kernel bitmap");
-    int per_sm = heavy_max_blocks_per_sm(block, smem);
+    // the exact form (a shared bit per net) unless that bitmap costs resident CTAs
+    const size_t smem_s = heavy_smem_bytes(mnode, ml, mn, false), smem_x = heavy_smem_bytes(mnode, ml, mn, true);
+    if (smem_s > 220 * 1024) return fail(ctx, RTLFS_E_ARG, "design too large for the heavy kernel bitmap");
+    const int per_sm_s = heavy_max_blocks_per_sm(block, smem_s, false);
+    const int per_sm_x = smem_x <= 220 * 1024 ? heavy_max_blocks_per_sm(block, smem_x, true) : 0;
+    const bool exact = form == 1 ? per_sm_x > 0 : form == 2 ? false : per_sm_x >= per_sm_s;
+    const int per_sm = exact ? per_sm_x : per_sm_s;
     if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "heavy kernel cannot be resident with block %d", block);
+    ctx->heavy_exact = exact;
+    if (exact) {
+        ctx->stamps_stale = true;   // its 8-byte values overwrite stamp fields
+    }
     int slots = want_slots > 0 ? want_slots : per_sm * ctx->n_sm;
     slots = std::min(slots, per_sm * ctx->n_sm);
     const bool grow = slots > (int)ctx->heavy_slots || mn > ctx->hs_net || mr > ctx->hs_reg;
     if (grow) {
-        ctx->h_fval.release(); ctx->h_regr.release(); ctx->h_regv.release();
+        ctx->h_fval.release(); ctx->h_regr.release(); ctx->h_regv.release(); ctx->h_stamp.release();
         CU(ctx->h_fval.reserve((size_t)slots * mn));
+        CU(ctx->h_stamp.reserve((size_t)slots));
+        ctx->stamps_stale = true;   // fresh memory: zeroed below before a stamped run
         CU(ctx->h_regr.reserve((size_t)slots * 2 * mr));
         CU(ctx->h_regv.reserve((size_t)slots * 2 * mr));
         ctx->heavy_slots = slots; ctx->hs_net = mn; ctx->hs_reg = mr;
     }
     ctx->hs_node = mnode; ctx->hs_lv = ml;
     ctx->heavy_grid = (uint32_t)slots;
+    if (!exact && ctx->stamps_stale) {
+        // stamp 0 is never current: zeroed entries and counters start every slot clean
+        // (on the main stream, which every heavy launch of the campaign waits behind)
+        CU(cudaMemsetAsync(ctx->h_fval.p, 0, ctx->h_fval.n * sizeof(HeavyVal), ctx->s_main));
+        CU(cudaMemsetAsync(ctx->h_stamp.p, 0, ctx->h_stamp.n * sizeof(uint32_t), ctx->s_main));
+        ctx->stamps_stale = false;
+    }
     return RTLFS_OK;
 }
 
 HeavyScratch heavy_view(rtlfs_ctx *ctx) {
     HeavyScratch s{};
     s.fval = ctx->h_fval.p;
+    s.stamp = ctx->h_stamp.p;
     s.reg_r = ctx->h_regr.p; s.reg_v = ctx->h_regv.p;
     s.max_net = ctx->hs_net; s.max_reg = ctx->hs_reg; s.max_node = ctx->hs_node;
+    s.exact = ctx->heavy_exact ? 1u : 0u;
     s.max_levels = ctx->hs_lv;
     return s;
 }
@@ -1031,7 +1054,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         rc = ensure_sched_buffers(ctx);
         if (rc != RTLFS_OK) return rc;
     }
-    rc = ensure_heavy_scratch(ctx, hblock, o.heavy_ctas);
+    if (o.heavy_form < 0 || o.heavy_form > 2) return fail(ctx, RTLFS_E_ARG, "heavy_form must be 0, 1 or 2");
+    rc = ensure_heavy_scratch(ctx, hblock, o.heavy_ctas, o.heavy_form);
     if (rc != RTLFS_OK) return rc;
     rc = prepare_good(ctx);
     if (rc != RTLFS_OK) return rc;
@@ -1306,7 +1330,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                               ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
                               ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,
                               ctx->d_bit.p, ctx->d_val.p, ctx->d_fdesign.p, ctx->p_cycle, ctx->p_port,
-                              ctx->p_det, ctx->p_load, ctx->h_fval.p, ctx->h_regr.p, ctx->h_regv.p,
+                              ctx->p_det, ctx->p_load, ctx->h_fval.p, ctx->h_stamp.p, ctx->h_regr.p, ctx->h_regv.p,
                               ctx->d_X.p, ctx->d_heur.p, ctx->d_pred.p, ctx->d_mm.p, ctx->d_hist.p,
                               ctx->d_wb.p, ctx->d_static_ptrs.p, ctx->w_st_nreg.p, ctx->w_st_r.p,
                               ctx->w_st_v.p, ctx->w_live0.p, ctx->w_live1.p, ctx->w_cnt32.p, ctx->w_cnt64.p,
@@ -1316,7 +1340,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
-                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv});
+                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv, (uint64_t)ctx->heavy_exact});
         for (int lc = 1; lc < 5; ++lc)
             key.insert(key.end(), {(uint64_t)g.n_cl[lc], (uint64_t)g.smem_cl[lc],
                                    (uint64_t)(uintptr_t)ctx->d_list_cl[lc].p});

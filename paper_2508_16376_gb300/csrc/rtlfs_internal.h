@@ -135,8 +135,8 @@ struct Queues {
     unsigned long long *counters;   // [0] node evaluations, [1] fault-cycles simulated
 };
 
-// Words of the heavy kernel's net bitmap remembered for clearing; beyond this many the
-// whole bitmap is cleared at the end of the cycle.
+// Exact form of the heavy kernel: words of its net bitmap remembered for clearing; beyond
+// this many the whole bitmap is cleared at the end of the cycle.
 constexpr uint32_t HEAVY_DLIST = 128;
 // Dirty nodes of one level a heavy CTA gathers into a list and splits over its threads;
 // a level with more is walked word by word.
@@ -148,11 +148,24 @@ constexpr uint32_t HEAVY_FRANGE = 64;
 constexpr uint32_t HEAVY_INLINE_FANOUT = 16;
 
 // Per-slot scratch of the heavy kernel (one slot per resident CTA).
+// A heavy slot's faulty value of a net, valid in the cycle whose stamp it carries (a
+// slot's stamps only grow, so nothing is cleared between cycles or faults).
+struct __align__(16) HeavyVal {
+    uint64_t v;
+    uint32_t stamp;
+    uint32_t pad;
+};
+
 struct HeavyScratch {
-    uint64_t *fval;      // [slots][max_net] faulty values of the nets that differ
+    HeavyVal *fval;      // [slots][max_net] faulty values of the nets that differ
+    uint32_t *stamp;     // [slots] last stamp each slot used
     uint32_t *reg_r;     // [slots][2][max_reg]
     uint64_t *reg_v;     // [slots][2][max_reg]
     uint32_t max_net, max_reg, max_node, max_levels;
+    // 1: the exact form -- a shared-memory bit per net marks the faulty values (8-byte values
+    // at the start of each slot's array); 0: the stamped form (a small shared filter and
+    // per-entry cycle stamps), chosen when the bitmap would cost resident CTAs
+    uint32_t exact;
 };
 
 // ---- windowed campaign (cycles processed in windows [t0, t1) by every live fault) ------
@@ -240,13 +253,13 @@ cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int 
                          int grid, cudaStream_t stream);
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream);
-size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net);
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net, bool exact);
 cudaError_t launch_plain(const DevDesign *d_designs, uint32_t design, DevFaults f,
                          uint32_t first, uint32_t count, uint64_t *fval, uint32_t *stamp,
                          uint32_t *qstamp, uint32_t *heap, uint32_t *reg_r, uint64_t *reg_v,
                          uint32_t stride_net, uint32_t stride_node, uint32_t stride_reg,
                          cudaStream_t stream);
 int light_max_blocks_per_sm(int cap, int block);
-int heavy_max_blocks_per_sm(int block, size_t smem);
+int heavy_max_blocks_per_sm(int block, size_t smem, bool exact);
 
 }  // namespace rtlfs

@@ -449,8 +449,10 @@ __device__ __forceinline__ uint32_t next_active(const uint64_t *__restrict__ fac
 // ===================================================================================
 // Heavy kernel: one CTA per fault (by default a single warp). Shared memory holds a bitmap
 // over the nodes (dirty: some operand differs), the number of dirty nodes per level (so an
-// empty level costs one shared read), a bitmap over the nets (differs this cycle) and a
-// ring of fan-out ranges to expand. Differing values live in per-slot global scratch.
+// empty level costs one shared read) and a ring of fan-out ranges to expand. Differing
+// values live in per-slot global scratch beside the stamp of the cycle that wrote them: an
+// operand read fetches that entry and the good value together and keeps the faulty one
+// when its stamp is the current cycle's, so nothing needs clearing between cycles.
 // Each level runs in up to three phases: (0) the level's dirty nodes are gathered from the
 // bitmap into a shared list, so they split evenly over the threads however they cluster
 // in the bitmap's words; (1) the threads evaluate them, and a kept net marks its consumers
@@ -462,6 +464,7 @@ __device__ __forceinline__ uint32_t next_active(const uint64_t *__restrict__ fac
 // come from and where a survivor's state goes.
 // ===================================================================================
 constexpr uint32_t HEAVY_PREFETCH = 4;
+constexpr uint32_t HEAVY_FILTER = 4096;   // bits of the kept-net filter (stamped form)
 
 // Shared scalars of one heavy CTA.
 struct HeavyVars {
@@ -470,7 +473,7 @@ struct HeavyVars {
     uint32_t nreg_new;         // register diffs latched this cycle
     uint32_t minport;          // lowest output port that differs this cycle
     uint32_t site_seeded;      // a register diff already covered the fault site
-    uint32_t nd;               // words of the net bitmap to clear
+    uint32_t nd;               // exact form: words of the net bitmap to clear
     uint32_t nfr;              // fan-out ranges appended this cycle
     uint32_t nl;               // dirty nodes gathered for the current level
 };
@@ -479,37 +482,49 @@ struct HeavyVars {
 struct HeavySmem {
     uint32_t *bm;                 // [nwn] dirty nodes
     uint32_t *cnt;                // [max_levels] dirty nodes per level
-    uint32_t *dbm;                // [nwd] nets that differ this cycle
-    uint32_t *dlist;              // [HEAVY_DLIST] words of dbm to clear
     uint32_t *nlist;              // [HEAVY_NLIST] dirty nodes of the current level
+    // stamped form: nets kept this cycle, by net id modulo HEAVY_FILTER (a clear bit: the
+    // net holds its good value; a set bit: read the stamped entry)
+    uint32_t *flt;                // [HEAVY_FILTER / 32]
+    // exact form: a bit per net (differs this cycle) and the words to clear after it
+    uint32_t *dbm;                // [nwd]
+    uint32_t *dlist;              // [HEAVY_DLIST]
     uint2 *frange;                // [HEAVY_FRANGE] fan-out ranges (8-byte aligned)
     unsigned long long *lvm;      // [nlw] one bit per level that has dirty nodes
     uint32_t nwd, nlw;
 };
 
+template <bool EXACT>
 __device__ __forceinline__ HeavySmem heavy_layout(uint32_t *hsm, const HeavyScratch &S) {
     HeavySmem m;
-    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
-    m.nwd = nwd;
+    const uint32_t nwn = (S.max_node + 31) / 32;
+    m.nwd = (S.max_net + 31) / 32;
     m.nlw = (S.max_levels + 63) / 64;
     m.bm = hsm;
     m.cnt = m.bm + nwn;
-    m.dbm = m.cnt + S.max_levels;
-    m.dlist = m.dbm + nwd;
-    m.nlist = m.dlist + HEAVY_DLIST;
-    const size_t fr_words = ((size_t)nwn + S.max_levels + nwd + HEAVY_DLIST + HEAVY_NLIST + 1) & ~(size_t)1;
+    m.nlist = m.cnt + S.max_levels;
+    m.flt = m.nlist + HEAVY_NLIST;
+    m.dbm = m.flt + (EXACT ? 0 : HEAVY_FILTER / 32);
+    m.dlist = m.dbm + (EXACT ? m.nwd : 0);
+    const size_t side = EXACT ? (size_t)m.nwd + HEAVY_DLIST : HEAVY_FILTER / 32;
+    const size_t fr_words = ((size_t)nwn + S.max_levels + HEAVY_NLIST + side + 1) & ~(size_t)1;
     m.frange = reinterpret_cast<uint2 *>(hsm + fr_words);
     m.lvm = reinterpret_cast<unsigned long long *>(m.frange + HEAVY_FRANGE);
     return m;
 }
 
 // Zero the bitmaps and counters once per CTA; every fault leaves them zero again.
+template <bool EXACT>
 __device__ __forceinline__ void heavy_zero(const HeavySmem &m, const HeavyScratch &S, HeavyVars &V) {
     const uint32_t tid = threadIdx.x, B = blockDim.x;
-    const uint32_t nwn = (S.max_node + 31) / 32, nwd = (S.max_net + 31) / 32;
+    const uint32_t nwn = (S.max_node + 31) / 32;
     for (uint32_t i = tid; i < nwn; i += B) m.bm[i] = 0;
     for (uint32_t i = tid; i < S.max_levels; i += B) m.cnt[i] = 0;
-    for (uint32_t i = tid; i < nwd; i += B) m.dbm[i] = 0;
+    if (EXACT) {
+        for (uint32_t i = tid; i < m.nwd; i += B) m.dbm[i] = 0;
+    } else {
+        for (uint32_t i = tid; i < HEAVY_FILTER / 32; i += B) m.flt[i] = 0;
+    }
     for (uint32_t i = tid; i < m.nlw; i += B) m.lvm[i] = 0;
     if (tid == 0) { V.nfr = 0; V.nl = 0; V.load = 0; }
 }
@@ -541,10 +556,11 @@ struct HeavyRun {
 // reaches tend. Cycles with no register diff and an inactive site are skipped without
 // work. V.load accumulates the node evaluations; the caller zeroes it per fault. Every
 // thread of the CTA calls this together and leaves the shared bitmaps zero.
+template <bool EXACT>
 __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFaults &f, uint32_t fid,
                                                 uint32_t tend, unsigned long long budget,
-                                                const HeavySmem &sm, HeavyVars &V, uint64_t *fval,
-                                                uint32_t *regR, uint64_t *regV, uint32_t max_reg,
+                                                const HeavySmem &sm, HeavyVars &V, HeavyVal *fval, uint32_t &stamp,
+                                                uint32_t *regR, uint64_t *regV, uint32_t max_reg, uint32_t max_net,
                                                 HeavyRun &r) {
     const uint32_t tid = threadIdx.x, B = blockDim.x;
     const uint32_t lane = tid & 31u, warp = tid >> 5;
@@ -559,7 +575,7 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
     const uint32_t site = fs.site;
     const uint32_t bit = f.bit[fid];
     const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
-    uint32_t *const bm = sm.bm, *const cnt = sm.cnt, *const dbm = sm.dbm;
+    uint32_t *const bm = sm.bm, *const cnt = sm.cnt;
     unsigned long long *const lvm = sm.lvm;
     const uint32_t nlw = sm.nlw;
     const bool nodrop = f.mism != nullptr;
@@ -612,11 +628,15 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
     // A net that differs this cycle: its value, its flag, a detecting port, and the
     // registers it drives whose latched value differs too (into half nb).
     auto keep_value = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni, uint32_t nb) {
-        fval[net] = v;
-        const uint32_t wbit = 1u << (net & 31u);
-        if (!atomicOr(&dbm[net >> 5], wbit)) {   // first bit of this word: remember the word
-            const uint32_t k = atomicAdd(&V.nd, 1u);
-            if (k < HEAVY_DLIST) sm.dlist[k] = net >> 5;
+        if (EXACT) {
+            reinterpret_cast<uint64_t *>(fval)[net] = v;
+            if (!atomicOr(&sm.dbm[net >> 5], 1u << (net & 31u))) {   // first bit of the word
+                const uint32_t k = atomicAdd(&V.nd, 1u);
+                if (k < HEAVY_DLIST) sm.dlist[k] = net >> 5;
+            }
+        } else {
+            reinterpret_cast<uint4 *>(fval)[net] = make_uint4((uint32_t)v, (uint32_t)(v >> 32), stamp, 0u);
+            atomicOr(&sm.flt[(net / 32u) % (HEAVY_FILTER / 32u)], 1u << (net & 31u));
         }
         const uint32_t p = ni_port(ni.w);
         if (p != NI_NO_PORT) atomicMin(&V.minport, p);
@@ -644,7 +664,12 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
         }
     };
     auto lookup = [&](uint32_t x) -> uint64_t {
-        if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
+        if (EXACT) {
+            if ((sm.dbm[x >> 5] >> (x & 31u)) & 1u) return reinterpret_cast<const uint64_t *>(fval)[x];
+        } else if ((sm.flt[(x / 32u) % (HEAVY_FILTER / 32u)] >> (x & 31u)) & 1u) {
+            const uint4 e = reinterpret_cast<const uint4 *>(fval)[x];   // kept this cycle, or a
+            if (e.z == stamp) return ((uint64_t)e.y << 32) | e.x;     // net sharing its bit
+        }
         return __ldg(gcol + (size_t)x * T + t);
     };
 
@@ -684,6 +709,13 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
         const uint32_t nb = cur ^ 1u;
         if (tid == 0) { V.nreg_new = 0; V.minport = NI_NO_PORT; V.site_seeded = 0; V.nd = 0; V.nfr = 0; }
         fr_begin = 0;
+        if (!EXACT) {
+            if (++stamp == 0u) {   // the slot's stamps wrapped: forget every old entry once
+                for (uint32_t i = tid; i < max_net; i += B) fval[i].stamp = 0u;
+                stamp = 1u;
+            }
+            for (uint32_t i = tid; i < HEAVY_FILTER / 32; i += B) sm.flt[i] = 0u;
+        }
         __syncthreads();
 
         // registers that carry a difference into this cycle
@@ -798,12 +830,13 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
         }
         if (my_load) atomicAdd(&V.load, (unsigned long long)my_load);
         __syncthreads();
-        // clear the net bitmap for the next cycle
-        const uint32_t nd = V.nd;
-        if (nd <= HEAVY_DLIST) {
-            for (uint32_t k = tid; k < nd; k += B) dbm[sm.dlist[k]] = 0;
-        } else {
-            for (uint32_t i = tid; i < sm.nwd; i += B) dbm[i] = 0;
+        if (EXACT) {   // clear the net bitmap for the next cycle
+            const uint32_t nd = V.nd;
+            if (nd <= HEAVY_DLIST) {
+                for (uint32_t k = tid; k < nd; k += B) sm.dbm[sm.dlist[k]] = 0;
+            } else {
+                for (uint32_t i = tid; i < sm.nwd; i += B) sm.dbm[i] = 0;
+            }
         }
         if (V.minport != NI_NO_PORT && detect(V.minport)) break;
         nreg = V.nreg_new;
@@ -826,10 +859,11 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
 // prefix sum instead of shared atomics, the detecting port and the evaluation count kept
 // per lane and reduced once per cycle, and the level bitmap cleared once per cycle. Same
 // results and the same evaluation counts as heavy_run_fault.
+template <bool EXACT>
 __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const DevFaults &f, uint32_t fid,
                                                      uint32_t tend, unsigned long long budget,
-                                                     const HeavySmem &sm, HeavyVars &V, uint64_t *fval,
-                                                     uint32_t *regR, uint64_t *regV, uint32_t max_reg,
+                                                     const HeavySmem &sm, HeavyVars &V, HeavyVal *fval, uint32_t &stamp,
+                                                     uint32_t *regR, uint64_t *regV, uint32_t max_reg, uint32_t max_net,
                                                      HeavyRun &r) {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31u;
@@ -844,7 +878,7 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
     const uint32_t site = fs.site;
     const uint32_t bit = f.bit[fid];
     const uint64_t *__restrict__ scol = gcol + (size_t)site * T;
-    uint32_t *const bm = sm.bm, *const cnt = sm.cnt, *const dbm = sm.dbm;
+    uint32_t *const bm = sm.bm, *const cnt = sm.cnt;
     unsigned long long *const lvm = sm.lvm;
     const uint32_t nlw = sm.nlw;
     const bool nodrop = f.mism != nullptr;
@@ -892,11 +926,15 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
     };
     uint32_t pmin = NI_NO_PORT;   // this lane's lowest differing port in the cycle
     auto keep_value = [&](uint32_t net, uint64_t v, uint64_t g, uint4 ni, uint32_t nb) {
-        fval[net] = v;
-        const uint32_t wbit = 1u << (net & 31u);
-        if (!atomicOr(&dbm[net >> 5], wbit)) {
-            const uint32_t k = atomicAdd(&V.nd, 1u);
-            if (k < HEAVY_DLIST) sm.dlist[k] = net >> 5;
+        if (EXACT) {
+            reinterpret_cast<uint64_t *>(fval)[net] = v;
+            if (!atomicOr(&sm.dbm[net >> 5], 1u << (net & 31u))) {   // first bit of the word
+                const uint32_t k = atomicAdd(&V.nd, 1u);
+                if (k < HEAVY_DLIST) sm.dlist[k] = net >> 5;
+            }
+        } else {
+            reinterpret_cast<uint4 *>(fval)[net] = make_uint4((uint32_t)v, (uint32_t)(v >> 32), stamp, 0u);
+            atomicOr(&sm.flt[(net / 32u) % (HEAVY_FILTER / 32u)], 1u << (net & 31u));
         }
         pmin = min(pmin, ni_port(ni.w));
         uint32_t nr = ni_nreg(ni.w);
@@ -922,7 +960,12 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
         }
     };
     auto lookup = [&](uint32_t x) -> uint64_t {
-        if ((dbm[x >> 5] >> (x & 31u)) & 1u) return fval[x];
+        if (EXACT) {
+            if ((sm.dbm[x >> 5] >> (x & 31u)) & 1u) return reinterpret_cast<const uint64_t *>(fval)[x];
+        } else if ((sm.flt[(x / 32u) % (HEAVY_FILTER / 32u)] >> (x & 31u)) & 1u) {
+            const uint4 e = reinterpret_cast<const uint4 *>(fval)[x];   // kept this cycle, or a
+            if (e.z == stamp) return ((uint64_t)e.y << 32) | e.x;     // net sharing its bit
+        }
         return __ldg(gcol + (size_t)x * T + t);
     };
 
@@ -957,6 +1000,13 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
         if (lane == 0) { V.nreg_new = 0; V.nd = 0; V.nfr = 0; }
         fr_begin = 0;
         pmin = NI_NO_PORT;
+        if (!EXACT) {
+            if (++stamp == 0u) {   // the slot's stamps wrapped: forget every old entry once
+                for (uint32_t i = lane; i < max_net; i += 32) fval[i].stamp = 0u;
+                stamp = 1u;
+            }
+            for (uint32_t i = lane; i < HEAVY_FILTER / 32; i += 32) sm.flt[i] = 0u;
+        }
         __syncwarp();
 
         // registers that carry a difference into this cycle
@@ -1087,12 +1137,13 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
         const uint32_t minport = __reduce_min_sync(FULL, pmin);
         __syncwarp();
         for (uint32_t i = lane; i < nlw; i += 32) lvm[i] = 0;
-        // clear the net bitmap for the next cycle
-        const uint32_t nd = V.nd;
-        if (nd <= HEAVY_DLIST) {
-            for (uint32_t k = lane; k < nd; k += 32) dbm[sm.dlist[k]] = 0;
-        } else {
-            for (uint32_t i = lane; i < sm.nwd; i += 32) dbm[i] = 0;
+        if (EXACT) {   // clear the net bitmap for the next cycle
+            const uint32_t nd = V.nd;
+            if (nd <= HEAVY_DLIST) {
+                for (uint32_t k = lane; k < nd; k += 32) sm.dbm[sm.dlist[k]] = 0;
+            } else {
+                for (uint32_t i = lane; i < sm.nwd; i += 32) sm.dbm[i] = 0;
+            }
         }
         if (minport != NI_NO_PORT && detect(minport)) break;
         nreg = V.nreg_new;
@@ -1118,19 +1169,20 @@ __device__ __forceinline__ void hsync() {
     if (WARP) __syncwarp(); else __syncthreads();
 }
 
-template <bool WARP>
+template <bool WARP, bool EXACT>
 __global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_n_items;
-    const HeavySmem sm = heavy_layout(hsm, S);
+    const HeavySmem sm = heavy_layout<EXACT>(hsm, S);
     const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
-    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
+    HeavyVal *fval = S.fval + (size_t)slot * S.max_net;
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
-    heavy_zero(sm, S, V);
+    uint32_t stamp = EXACT ? 0u : S.stamp[slot];   // the same in every thread, advanced together
+    heavy_zero<EXACT>(sm, S, V);
     hsync<WARP>();
 
     for (;;) {
@@ -1151,8 +1203,8 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         if (tid == 0) V.load = 0;
         hsync<WARP>();
         HeavyRun r{it.t, it.nreg, 0, 0, -1, -1, 0};
-        if (WARP) heavy_run_fault_warp(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
-        else heavy_run_fault(D, f, fid, D.T, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        if (WARP) heavy_run_fault_warp<EXACT>(D, f, fid, D.T, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
+        else heavy_run_fault<EXACT>(D, f, fid, D.T, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
         hsync<WARP>();
         if (tid == 0) {
             f.load[fid] += V.load;
@@ -1169,23 +1221,25 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         }
         hsync<WARP>();
     }
+    if (!EXACT && threadIdx.x == 0) S.stamp[slot] = stamp;   // the next launch continues from it
 }
 
 // Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
 // from the last window and those promoted in this one; survivors carry their register
 // diffs to the next window through the pool.
-template <bool WARP>
+template <bool WARP, bool EXACT>
 __global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
     __shared__ unsigned long long s_item, s_off;
-    const HeavySmem sm = heavy_layout(hsm, S);
+    const HeavySmem sm = heavy_layout<EXACT>(hsm, S);
     const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
-    uint64_t *fval = S.fval + (size_t)slot * S.max_net;
+    HeavyVal *fval = S.fval + (size_t)slot * S.max_net;
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
-    heavy_zero(sm, S, V);
+    uint32_t stamp = EXACT ? 0u : S.stamp[slot];   // the same in every thread, advanced together
+    heavy_zero<EXACT>(sm, S, V);
     hsync<WARP>();
 
     // written before this launch by earlier work on the stream: the same in every thread
@@ -1212,8 +1266,8 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         if (tid == 0) V.load = 0;
         hsync<WARP>();
         HeavyRun r{t_start, nreg0, 0, 0, -1, -1, 0};
-        if (WARP) heavy_run_fault_warp(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
-        else heavy_run_fault(D, f, fid, tend, q.fault_budget, sm, V, fval, regR, regV, S.max_reg, r);
+        if (WARP) heavy_run_fault_warp<EXACT>(D, f, fid, tend, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
+        else heavy_run_fault<EXACT>(D, f, fid, tend, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
         hsync<WARP>();
         const bool carry = r.status == 0 && tend < D.T;   // alive at the end of the window
         if (carry) {
@@ -1247,6 +1301,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         }
         hsync<WARP>();
     }
+    if (!EXACT && threadIdx.x == 0) S.stamp[slot] = stamp;   // the next launch continues from it
 }
 
 // ===================================================================================
@@ -1915,16 +1970,25 @@ cudaError_t launch_light_window(const DevDesign *d_designs, DevFaults f, WinLigh
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
-size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net) {
-    size_t words = (size_t)(max_node + 31) / 32 + max_levels + (max_net + 31) / 32 + HEAVY_DLIST + HEAVY_NLIST;
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net, bool exact) {
+    const size_t side = exact ? (size_t)(max_net + 31) / 32 + HEAVY_DLIST : HEAVY_FILTER / 32;
+    size_t words = (size_t)(max_node + 31) / 32 + max_levels + HEAVY_NLIST + side;
     words = (words + 1) & ~(size_t)1;   // 8-byte alignment of the range list
     return words * sizeof(uint32_t) + HEAVY_FRANGE * sizeof(uint2) +
            (size_t)((max_levels + 63) / 64) * sizeof(unsigned long long);
 }
 
-int heavy_max_blocks_per_sm(int block, size_t smem) {
+static const void *heavy_fn(bool window, int block, bool exact) {
+    if (window)
+        return block == 32 ? (exact ? (const void *)heavy_window_kernel<true, true> : (const void *)heavy_window_kernel<true, false>)
+                           : (exact ? (const void *)heavy_window_kernel<false, true> : (const void *)heavy_window_kernel<false, false>);
+    return block == 32 ? (exact ? (const void *)heavy_kernel<true, true> : (const void *)heavy_kernel<true, false>)
+                       : (exact ? (const void *)heavy_kernel<false, true> : (const void *)heavy_kernel<false, false>);
+}
+
+int heavy_max_blocks_per_sm(int block, size_t smem, bool exact) {
     int n = 0;
-    const void *fn = block == 32 ? (const void *)heavy_window_kernel<true> : (const void *)heavy_window_kernel<false>;
+    const void *fn = heavy_fn(true, block, exact);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem);
     return n;
@@ -1932,8 +1996,8 @@ int heavy_max_blocks_per_sm(int block, size_t smem) {
 
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream) {
-    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net);
-    const void *fn = block == 32 ? (const void *)heavy_kernel<true> : (const void *)heavy_kernel<false>;
+    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net, s.exact != 0);
+    const void *fn = heavy_fn(false, block, s.exact != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_designs, (void *)&f, (void *)&q, (void *)&s};
@@ -1942,8 +2006,8 @@ cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, Heav
 
 cudaError_t launch_heavy_window(const DevDesign *d_designs, DevFaults f, WinHeavy w, HeavyScratch s,
                                 int block, int grid, cudaStream_t stream) {
-    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net);
-    const void *fn = block == 32 ? (const void *)heavy_window_kernel<true> : (const void *)heavy_window_kernel<false>;
+    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net, s.exact != 0);
+    const void *fn = heavy_fn(true, block, s.exact != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_designs, (void *)&f, (void *)&w, (void *)&s};

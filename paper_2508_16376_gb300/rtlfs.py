@@ -43,7 +43,8 @@ class rtlfs_run_opts(ctypes.Structure):
                 ("heavy_frac", ctypes.c_float), ("use_graph", ctypes.c_int32),
                 ("fault_budget", ctypes.c_uint64), ("light_cap", ctypes.c_int32),
                 ("window", ctypes.c_int32), ("no_drop", ctypes.c_int32),
-                ("good_cluster", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 4)]
+                ("heavy_form", ctypes.c_int32), ("good_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class rtlfs_stats(ctypes.Structure):

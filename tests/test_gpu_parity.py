@@ -81,6 +81,8 @@ def test_good_trace_global_memory_path():
 
 OPTION_SETS = [
     dict(),
+    dict(heavy_frac=1.0, heavy_form=2),
+    dict(heavy_frac=0.3, heavy_form=2, heavy_block=128),
     dict(scheduler=rtlfs.SCHED_PLAIN),
     dict(heavy_frac=0.05),
     dict(heavy_frac=1.0),
@@ -153,7 +155,8 @@ def test_fsm_design_all_faults_with_promotion(seed):
     got = gpu_run(d, stim, u, want_load=True)
     assert_same(got, exp, "fsm")
     assert got[4]["promoted"] > 0
-    for kw in (dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN), dict(heavy_frac=1.0)):
+    for kw in (dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN), dict(heavy_frac=1.0),
+               dict(heavy_frac=1.0, heavy_form=2), dict(heavy_frac=1.0, heavy_form=1, window=64)):
         assert_same(gpu_run(d, stim, u, **kw), exp, f"fsm {kw}")
 
 
@@ -210,6 +213,25 @@ def test_duplicate_faults():
         assert np.array_equal(cyc[:300], cyc[300 * k:300 * (k + 1)])
 
 
+def test_heavy_forms_alternate_on_one_context():
+    """The exact and stamped heavy forms share their scratch: alternating them in one
+    context (and windows with one pass) gives the same results and loads every time."""
+    d = small_fsm_design(29)
+    stim = synth.stimulus(d, 260, 29, 0.1)
+    u = synth.sample_faults(d, 2500, 29)
+    exp = oracle.fault_sim(d, stim, u, threads=16)
+    with Simulator(0) as sim:
+        sim.add(d, stim, u)
+        ref = None
+        for kw in (dict(heavy_form=1), dict(heavy_form=2), dict(heavy_form=1, window=64),
+                   dict(heavy_form=2, window=64), dict(heavy_form=2), dict(heavy_form=1)):
+            res, loads = sim.run(want_load=True, heavy_frac=1.0, **kw)
+            assert_same(split(res[0]), exp, str(kw))
+            if ref is None:
+                ref = loads[0]
+            assert np.array_equal(loads[0], ref), str(kw)
+
+
 def test_loads_are_schedule_independent():
     """The recorded propagation load of a fault is a property of the fault, not of the
     kernel that simulated it (the same nodes are evaluated in the same cycles)."""
@@ -218,7 +240,8 @@ def test_loads_are_schedule_independent():
     u = synth.sample_faults(d, 2000, 23)
     a = gpu_run(d, stim, u, want_load=True, heavy_frac=0.0)[3]
     b = gpu_run(d, stim, u, want_load=True, heavy_frac=1.0)[3]
-    assert np.array_equal(a, b)
+    c = gpu_run(d, stim, u, want_load=True, heavy_frac=1.0, heavy_form=2)[3]
+    assert np.array_equal(a, b) and np.array_equal(a, c)
     assert a.sum() > 0
 
 
@@ -329,7 +352,7 @@ def test_windowed_matches_oracle(window):
     u = synth.sample_faults(d, 3000, 27)
     exp = oracle.fault_sim(d, stim, u, threads=16)
     for kw in (dict(), dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN, light_cap=1),
-               dict(heavy_frac=1.0)):
+               dict(heavy_frac=1.0), dict(heavy_frac=1.0, heavy_form=2), dict(heavy_form=2, heavy_block=64)):
         got = gpu_run(d, stim, u, want_load=True, window=window, **kw)
         assert_same(got, exp, f"window {window} {kw}")
     ref = gpu_run(d, stim, u, want_load=True)
