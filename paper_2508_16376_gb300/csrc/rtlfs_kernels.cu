@@ -285,6 +285,8 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
     const uint4 *__restrict__ creg = D.cl_reg + D.cl_reg_off[rank];
     const uint32_t NR = D.cl_reg_off[rank + 1] - D.cl_reg_off[rank];
     const uint32_t base = smem_u32(gsm);
+    __shared__ uint32_t s_fail;   // a staging wait of this CTA ran out (set once, read after barriers)
+    if (tid == 0) s_fail = 0u;
     for (uint32_t c = tid; c < NC; c += B) ch[c] = D.cl_chunk[c0 + c];
     if (tid == 0) {
         for (int b = 0; b < GOOD_NBUF; ++b)
@@ -350,11 +352,20 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
                 gsm[b.x + tid] = v;
                 row[IR + b.z + tid] = v;
             }
-            // every thread is done with this buffer (and every wait succeeded): refill it
-            if (!__syncthreads_and(staged) && !failed) { failed = true; f_kc = kc; f_buf = buf; f_par = par; }
+            // every thread is done with this buffer (and every wait succeeded): refill it. At
+            // a level's end the cluster barrier (which completes the level cluster-wide) is
+            // that barrier too, with a failed wait reported through a shared flag.
+            bool all_staged;
+            if (b.y & 0x80000000u) {
+                if (!staged) s_fail = 1u;
+                cluster_sync();
+                all_staged = s_fail == 0u;
+            } else {
+                all_staged = __syncthreads_and(staged);
+            }
+            if (!all_staged && !failed) { failed = true; f_kc = kc; f_buf = buf; f_par = par; }
             if (tid == 0 && !failed && kc + GOOD_NBUF < total) issue(buf);
             if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
-            if (b.y & 0x80000000u) cluster_sync();   // a level is complete cluster-wide
         }
         // latch: Q of cycle t+1 into the other bank
         for (uint32_t j = tid; j < NR; j += B) {
