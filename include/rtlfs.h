@@ -152,6 +152,13 @@ typedef struct {
                                 paper's evaluation protocol, Sec. V-A): the result keeps the
                                 first detection and rtlfs_mismatch_counts gives each fault's
                                 number of cycles with a differing output */
+    int32_t  stop_cycle;     /* windowed form, > 0: stop the campaign at this cycle (a multiple
+                                of `window`, below the longest stimulus) and keep its state for
+                                rtlfs_checkpoint_save; faults still being simulated report
+                                detected = RTLFS_PENDING */
+    int32_t  resume;         /* 1: continue the campaign from the checkpoint held by the context
+                                (made by a stopped run or rtlfs_checkpoint_load); the other
+                                options must match the stopped run's window and no_drop */
     int32_t  heavy_form;     /* heavy kernel's record of differing nets: 0 = auto (the
                                 exact one unless it costs resident CTAs), 1 = a shared-memory
                                 bit per net, 2 = a small shared filter plus cycle stamps on
@@ -163,7 +170,7 @@ typedef struct {
                                 shared memory, else one CTA over the global trace);
                                 1 = one CTA; 2, 4, 8 or 16 = clusters of that many CTAs
                                 (RTLFS_E_ARG when a design cannot run that way) */
-    uint32_t reserved[3];
+    uint32_t reserved[1];
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */
@@ -248,6 +255,24 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out_per_design);
 
 /* Counters and timings of the last rtlfs_run / rtlfs_run_plain. */
 int rtlfs_get_stats(const rtlfs_ctx *ctx, rtlfs_stats *out);
+
+/* Checkpoint and resume at a window boundary (no counterpart in the paper, which runs a
+ * campaign in one go). A run with stop_cycle = c leaves in the context everything the rest of
+ * the campaign needs: each fault's result so far, load and mismatch count, the register
+ * diffs of the faults still alive (light lanes and heavy CTAs alike), the campaign counters
+ * and each design's good-trace row at cycle c-1 (the good machine restarts from it). These
+ * calls move that state through a caller-owned buffer, e.g. to disk and into another
+ * process. A resumed campaign reaches the same results, loads and mismatch counts as an
+ * uninterrupted one.
+ *   rtlfs_checkpoint_size: bytes the current checkpoint takes (RTLFS_E_STATE: none held).
+ *   rtlfs_checkpoint_save: write it into buf[bytes] (RTLFS_E_ARG if bytes is too small).
+ *   rtlfs_checkpoint_load: take a checkpoint into a context holding the same designs,
+ *     stimuli and fault lists (RTLFS_E_ARG on a malformed buffer or a mismatch); the next
+ *     rtlfs_run with resume = 1 continues from it. */
+#define RTLFS_PENDING 254   /* rtlfs_result.detected of a fault still alive at stop_cycle */
+int rtlfs_checkpoint_size(rtlfs_ctx *ctx, uint64_t *bytes);
+int rtlfs_checkpoint_save(rtlfs_ctx *ctx, void *buf, uint64_t bytes);
+int rtlfs_checkpoint_load(rtlfs_ctx *ctx, const void *buf, uint64_t bytes);
 
 /* After an rtlfs_run with no_drop = 1: for each fault of the design (in list order), the
  * number of cycles in which some output port differs from the good machine (n-detection

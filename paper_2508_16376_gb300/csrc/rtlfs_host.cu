@@ -172,6 +172,18 @@ struct rtlfs_ctx {
     uint64_t *p_load = nullptr;
     size_t p_cap = 0;
     rtlfs_stats stats{};
+    // campaign state at a window boundary (host copy), see rtlfs_checkpoint_*
+    struct Checkpoint {
+        bool valid = false;
+        uint32_t window = 0;              // first window still to run
+        uint32_t W = 0, F = 0, nodrop = 0;
+        std::vector<uint32_t> T, n_net;   // per design
+        std::vector<uint8_t> det, st_nreg;
+        std::vector<int32_t> cycle, port;
+        std::vector<uint64_t> load, st_v, pool_v, heads, rows;
+        std::vector<uint32_t> mism, live, st_r, pool_r;
+        std::vector<HeavyCarry> carry;
+    } ck;
 };
 
 namespace {
@@ -862,8 +874,129 @@ int set_faults_impl(rtlfs_ctx *ctx, uint32_t design_id, uint32_t n_faults, bool 
     }
     D.f_site.swap(s); D.f_bit.swap(b); D.f_val.swap(v); D.f_port.swap(port); D.f_t0.swap(t0);
     ctx->faults_dirty = true;
+    ctx->ck.valid = false;
     ctx->err.clear();
     return RTLFS_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Whether the context can continue the checkpoint: same fault count, designs, stimulus
+// lengths, net counts, window and no-drop mode.
+int checkpoint_matches(rtlfs_ctx *ctx, const rtlfs_ctx::Checkpoint &c, uint32_t W, bool nodrop) {
+    if (!c.valid) return fail(ctx, RTLFS_E_STATE, "no checkpoint to resume from");
+    if (c.F != ctx->F || c.T.size() != ctx->designs.size())
+        return fail(ctx, RTLFS_E_ARG, "checkpoint was taken on other fault lists or designs");
+    for (size_t d = 0; d < ctx->designs.size(); ++d)
+        if (c.T[d] != ctx->designs[d]->T || c.n_net[d] != ctx->designs[d]->n_net)
+            return fail(ctx, RTLFS_E_ARG, "checkpoint design %zu differs from the context's", d);
+    if (c.W != W) return fail(ctx, RTLFS_E_ARG, "resume needs the checkpoint's window (%u)", c.W);
+    if (c.nodrop != (nodrop ? 1u : 0u)) return fail(ctx, RTLFS_E_ARG, "resume needs the checkpoint's no_drop mode");
+    return RTLFS_OK;
+}
+
+// Copy the campaign state after window w_end - 1 to the host (after the stream has drained).
+// pending[f] marks the faults still alive at the stop.
+int take_checkpoint(rtlfs_ctx *ctx, uint32_t nw, uint32_t w_end, uint32_t W, bool nodrop,
+                    std::vector<uint8_t> *pending) {
+    rtlfs_ctx::Checkpoint &c = ctx->ck;
+    const uint32_t F = ctx->F, wl = w_end - 1;
+    c = rtlfs_ctx::Checkpoint{};
+    c.window = w_end; c.W = W; c.F = F; c.nodrop = nodrop ? 1u : 0u;
+    for (Design *D : ctx->designs) { c.T.push_back(D->T); c.n_net.push_back(D->n_net); }
+    uint32_t n_live = 0, n_carry = 0;
+    unsigned long long pool_top = 0;
+    CU(cudaMemcpy(&n_live, ctx->w_cnt32.p + wl, 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&n_carry, ctx->w_cnt32.p + 2 * (size_t)nw + wl, 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&pool_top, ctx->w_cnt64.p + wl, 8, cudaMemcpyDeviceToHost));
+    if (n_live > F || n_carry > F || pool_top > ctx->w_pool_cap) return fail(ctx, RTLFS_E_CUDA, "inconsistent campaign counters");
+    auto get = [&](auto &v, const auto *src, size_t n) -> int {
+        v.resize(n);
+        if (n) CU(cudaMemcpy(v.data(), src, n * sizeof(v[0]), cudaMemcpyDeviceToHost));
+        return RTLFS_OK;
+    };
+    int r = RTLFS_OK;
+    if ((r = get(c.det, ctx->d_det.p, F)) || (r = get(c.cycle, ctx->d_cycle.p, F)) ||
+        (r = get(c.port, ctx->d_port.p, F)) || (r = get(c.load, ctx->d_load.p, F)) ||
+        (r = get(c.mism, ctx->d_mism.p, F)) || (r = get(c.st_nreg, ctx->w_st_nreg.p, F)) ||
+        (r = get(c.st_r, ctx->w_st_r.p, (size_t)F * LIGHT_KR)) || (r = get(c.st_v, ctx->w_st_v.p, (size_t)F * LIGHT_KR)) ||
+        (r = get(c.live, (wl & 1) ? ctx->w_live1.p : ctx->w_live0.p, n_live)) ||
+        (r = get(c.carry, (wl & 1) ? ctx->w_carry1.p : ctx->w_carry0.p, n_carry)) ||
+        (r = get(c.pool_r, (wl & 1) ? ctx->w_pool_r1.p : ctx->w_pool_r0.p, pool_top)) ||
+        (r = get(c.pool_v, (wl & 1) ? ctx->w_pool_v1.p : ctx->w_pool_v0.p, pool_top)) ||
+        (r = get(c.heads, ctx->d_heads.p, 8)))
+        return r;
+    // each design's good-trace row of the last cycle before the stop: the good machine's
+    // registers restart from it
+    const uint32_t cyc = w_end * W;
+    for (Design *D : ctx->designs) {
+        std::vector<uint64_t> row(D->n_net, 0);
+        if (cyc <= D->T && D->n_net)
+            CU(cudaMemcpy(row.data(), D->d_rows.p + (size_t)(cyc - 1) * D->n_net, (size_t)D->n_net * 8, cudaMemcpyDeviceToHost));
+        c.rows.insert(c.rows.end(), row.begin(), row.end());
+    }
+    pending->assign(F, 0);
+    for (uint32_t f : c.live) if (f < F) (*pending)[f] = 1;
+    for (const HeavyCarry &h : c.carry) if (h.fault < F) (*pending)[h.fault] = 1;
+    c.valid = true;
+    return RTLFS_OK;
+}
+
+// Put the checkpoint's state where window w_begin reads it (stream work on s_main, before the
+// first window's launches).
+int restore_checkpoint(rtlfs_ctx *ctx, uint32_t nw, uint32_t w_begin, uint32_t *prom_total) {
+    const rtlfs_ctx::Checkpoint &c = ctx->ck;
+    const uint32_t F = ctx->F, wp = w_begin - 1;
+    cudaStream_t s = ctx->s_main;
+    auto put = [&](auto *dst, const auto &v) -> int {
+        if (!v.empty()) CU(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, s));
+        return RTLFS_OK;
+    };
+    int r = RTLFS_OK;
+    if ((r = put(ctx->d_det.p, c.det)) || (r = put(ctx->d_cycle.p, c.cycle)) || (r = put(ctx->d_port.p, c.port)) ||
+        (r = put(ctx->d_load.p, c.load)) || (r = put(ctx->d_mism.p, c.mism)) || (r = put(ctx->w_st_nreg.p, c.st_nreg)) ||
+        (r = put(ctx->w_st_r.p, c.st_r)) || (r = put(ctx->w_st_v.p, c.st_v)) ||
+        (r = put((w_begin & 1) ? ctx->w_live0.p : ctx->w_live1.p, c.live)) ||
+        (r = put((w_begin & 1) ? ctx->w_carry0.p : ctx->w_carry1.p, c.carry)) ||
+        (r = put((w_begin & 1) ? ctx->w_pool_r0.p : ctx->w_pool_r1.p, c.pool_r)) ||
+        (r = put((w_begin & 1) ? ctx->w_pool_v0.p : ctx->w_pool_v1.p, c.pool_v)) ||
+        (r = put(ctx->d_heads.p, c.heads)))
+        return r;
+    (void)F;
+    // counts the first window reads: survivors, carries, and an empty promotion list
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(ctx->p_small + 13);
+    cnt[0] = (uint32_t)c.live.size();
+    cnt[1] = (uint32_t)c.carry.size();
+    CU(cudaMemcpyAsync(ctx->w_cnt32.p + wp, cnt + 0, 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ctx->w_cnt32.p + 2 * (size_t)nw + wp, cnt + 1, 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(ctx->w_cnt32.p + nw + wp, 0, 4, s));
+    CU(cudaMemsetAsync(prom_total, 0, 4, s));
+    const uint32_t cyc = w_begin * c.W;
+    size_t off = 0;
+    for (size_t d = 0; d < ctx->designs.size(); ++d) {
+        Design *D = ctx->designs[d];
+        if (cyc <= D->T && D->n_net)
+            CU(cudaMemcpyAsync(D->d_rows.p + (size_t)(cyc - 1) * D->n_net, c.rows.data() + off,
+                               (size_t)D->n_net * 8, cudaMemcpyHostToDevice, s));
+        off += D->n_net;
+    }
+    return RTLFS_OK;
+}
+
+// Checkpoint wire format: a header, per-design (T, n_net), then the arrays in a fixed order.
+constexpr char CK_MAGIC[8] = {'R', 'T', 'L', 'F', 'S', 'C', 'K', '1'};
+struct CkHeader {
+    char magic[8];
+    uint32_t n_designs, F, W, window, nodrop, n_live, n_carry, reserved;
+    uint64_t pool_top, n_rows;
+};
+
+template <typename Fn>
+void ck_fields(rtlfs_ctx::Checkpoint &c, Fn fn) {
+    fn(c.T); fn(c.n_net); fn(c.det); fn(c.cycle); fn(c.port); fn(c.load); fn(c.mism); fn(c.st_nreg);
+    fn(c.st_r); fn(c.st_v); fn(c.live); fn(c.carry); fn(c.pool_r); fn(c.pool_v); fn(c.heads); fn(c.rows);
 }
 
 }  // namespace
@@ -964,6 +1097,7 @@ int rtlfs_set_stimulus(rtlfs_ctx *ctx, uint32_t design_id, const uint64_t *input
     D.T = n_cycles;
     D.has_stim = true;
     D.trace_valid = false;
+    ctx->ck.valid = false;
     ctx->err.clear();
     return RTLFS_OK;
 }
@@ -1129,6 +1263,22 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         ci[2] = 0;
         ci[3] = 0;
     }
+    // Checkpoint options: the campaign runs windows [w_begin, w_end).
+    const bool stopping = o.stop_cycle > 0, resuming = o.resume != 0;
+    if (o.stop_cycle < 0) return fail(ctx, RTLFS_E_ARG, "stop_cycle must not be negative");
+    if ((stopping || resuming) && (!W || o.use_graph))
+        return fail(ctx, RTLFS_E_ARG, "stop_cycle and resume need the windowed form without graph replay");
+    if (stopping && ((uint32_t)o.stop_cycle % W != 0 || (uint32_t)o.stop_cycle >= Tmax))
+        return fail(ctx, RTLFS_E_ARG, "stop_cycle must be a multiple of window below the longest stimulus");
+    const uint32_t w_end = stopping ? (uint32_t)o.stop_cycle / W : nw;
+    uint32_t w_begin = 0;
+    if (resuming) {
+        int rc2 = checkpoint_matches(ctx, ctx->ck, W, nodrop);
+        if (rc2 != RTLFS_OK) return rc2;
+        w_begin = ctx->ck.window;
+        if (w_begin >= w_end) return fail(ctx, RTLFS_E_ARG, "stop_cycle is not after the checkpoint");
+        if (ctx->ck.pool_r.size() > ctx->w_pool_cap) return fail(ctx, RTLFS_E_ARG, "checkpoint pool exceeds capacity");
+    }
     const bool timed_windows = W && !o.use_graph;
     // Activation bitplane: built after the good trace (per window when windows are whole
     // multiples of 64 cycles); otherwise the kernels scan the good trace.
@@ -1148,7 +1298,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         uint32_t *prom_total = c32 + 3 * nw, *n_light0 = c32 + 3 * nw + 1, *zero = c32 + 3 * nw + 2;
         CU(cudaEventRecord(ev[0], ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
-        if (nodrop && F) {   // results are written at first detection; the rest stay undetected
+        if (nodrop && F && !resuming) {   // results are written at first detection; the rest stay undetected
             CU(cudaMemsetAsync(ctx->d_mism.p, 0, (size_t)F * sizeof(uint32_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->d_det.p, 0, (size_t)F, ctx->s_main));
             CU(cudaMemsetAsync(ctx->d_cycle.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
@@ -1158,16 +1308,20 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(cudaMemsetAsync(c64, 0, (3 * (size_t)nw + 1) * sizeof(unsigned long long), ctx->s_main));
         CU(cudaMemcpyAsync(prom_total, ctx->p_small + 10, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
-        if (F) {
+        if (F && !resuming) {
             CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->w_st_nreg.p, 0, F, ctx->s_main));
+        }
+        if (resuming) {
+            int r4 = restore_checkpoint(ctx, nw, w_begin, prom_total);
+            if (r4 != RTLFS_OK) return r4;
         }
         CU(cudaEventRecord(ctx->ev_wl, ctx->s_main));
         CU(cudaStreamWaitEvent(ctx->s_good, ctx->ev_wl, 0));
         CU(cudaStreamWaitEvent(ctx->s_heavy, ctx->ev_wl, 0));
         const uint32_t lblocks = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(((int64_t)F + lblock - 1) / lblock,
                                                                                   (int64_t)lgrid_cap));
-        for (uint32_t w = 0; w < nw; ++w) {
+        for (uint32_t w = w_begin; w < w_end; ++w) {
             const uint32_t t0 = w * W, t1 = std::min(t0 + W, Tmax);
             // good trace of the window
             int r3 = launch_good_lists(ctx, ctx->s_good, t0, t1, &launches);
@@ -1175,7 +1329,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             CU(launch_transpose_window(ctx->d_designs.p, (uint32_t)ctx->designs.size(), max_net, t0, t1, ctx->s_good));
             ++launches;
             if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, t0, t1, ctx->s_good)); ++launches; }
-            if (w == 0) CU(cudaEventRecord(ev[1], ctx->s_good));
+            if (w == w_begin) CU(cudaEventRecord(ev[1], ctx->s_good));
             CU(cudaEventRecord(ctx->ev_wg, ctx->s_good));
             // light kernel of the window (after the scheduler for the first one)
             CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_wg, 0));
@@ -1380,8 +1534,15 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     }
     const unsigned long long *heads = ctx->p_small;
     const uint32_t *cnts = reinterpret_cast<const uint32_t *>(ctx->p_small + 8);
-    for (Design *D : ctx->designs) D->trace_valid = true;
-    ctx->mism_valid = nodrop;
+    for (Design *D : ctx->designs) D->trace_valid = !stopping && !resuming;
+    ctx->mism_valid = nodrop && !stopping;
+    std::vector<uint8_t> pending;
+    if (stopping) {
+        rc = take_checkpoint(ctx, nw, w_end, W, nodrop, &pending);
+        if (rc != RTLFS_OK) return rc;
+    } else {
+        ctx->ck.valid = false;   // the campaign ran to its end
+    }
 
     // Scatter results and counters.
     rtlfs_stats &st = ctx->stats;
@@ -1393,7 +1554,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         st.total_ms = ev_ms(ev[0], ev[5]);
         st.good_ms = ev_ms(ev[0], ev[3]);
         st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
-        for (uint32_t w = 0; w < nw; ++w) {
+        for (uint32_t w = w_begin; w < w_end; ++w) {
             st.light_ms += ev_ms(ctx->ev_win[w], ctx->ev_win[nw + w]);
             st.heavy_ms += ev_ms(ctx->ev_win[2 * nw + w], ctx->ev_win[3 * nw + w]);
         }
@@ -1409,8 +1570,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     st.promoted = cnts[1];
     st.heavy_initial = cnts[0];
     if (W) {   // the windowed form reports the promotion list's total (initial + promoted)
-        st.heavy_initial = n_heavy;
-        st.promoted = cnts[0] - n_heavy;
+        st.heavy_initial = resuming ? 0 : n_heavy;   // a resumed run's list holds promotions only
+        st.promoted = cnts[0] - st.heavy_initial;
     }
     st.n_launches = launches;
     st.light_evals = heads[4];
@@ -1423,7 +1584,9 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         uint64_t *ld = out_load ? out_load[d] : nullptr;
         for (uint32_t i = ctx->f_first[d]; i < ctx->f_first[d + 1]; ++i) {
             const uint32_t k = i - ctx->f_first[d];
-            const uint8_t det = ctx->p_det[i];
+            const bool pend = !pending.empty() && pending[i];
+            const uint8_t det = pend ? (uint8_t)RTLFS_PENDING : ctx->p_det[i];
+            if (pend) { ctx->p_cycle[i] = -1; ctx->p_port[i] = -1; }
             if (r) {
                 r[k].detected = det;
                 r[k].cycle = ctx->p_cycle[i];
@@ -1744,4 +1907,74 @@ int rtlfs_design_info(const rtlfs_ctx *ctx, uint32_t design_id, uint32_t *n_nets
     return RTLFS_OK;
 }
 
+
+int rtlfs_checkpoint_size(rtlfs_ctx *ctx, uint64_t *bytes) {
+    if (!ctx || !bytes) return RTLFS_E_ARG;
+    if (!ctx->ck.valid) return fail(ctx, RTLFS_E_STATE, "no checkpoint held");
+    uint64_t n = sizeof(CkHeader);
+    ck_fields(ctx->ck, [&](auto &v) { n += v.size() * sizeof(v[0]); });
+    *bytes = n;
+    return RTLFS_OK;
+}
+
+int rtlfs_checkpoint_save(rtlfs_ctx *ctx, void *buf, uint64_t bytes) {
+    uint64_t need = 0;
+    int rc = rtlfs_checkpoint_size(ctx, &need);
+    if (rc != RTLFS_OK) return rc;
+    if (!buf || bytes < need) return fail(ctx, RTLFS_E_ARG, "checkpoint buffer too small (%llu bytes needed)", (unsigned long long)need);
+    rtlfs_ctx::Checkpoint &c = ctx->ck;
+    CkHeader h{};
+    memcpy(h.magic, CK_MAGIC, 8);
+    h.n_designs = (uint32_t)c.T.size(); h.F = c.F; h.W = c.W; h.window = c.window; h.nodrop = c.nodrop;
+    h.n_live = (uint32_t)c.live.size(); h.n_carry = (uint32_t)c.carry.size();
+    h.pool_top = c.pool_r.size(); h.n_rows = c.rows.size();
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    ck_fields(c, [&](auto &v) {
+        if (!v.empty()) memcpy(p, v.data(), v.size() * sizeof(v[0]));
+        p += v.size() * sizeof(v[0]);
+    });
+    ctx->err.clear();
+    return RTLFS_OK;
+}
+
+int rtlfs_checkpoint_load(rtlfs_ctx *ctx, const void *buf, uint64_t bytes) {
+    if (!ctx) return RTLFS_E_ARG;
+    if (!buf || bytes < sizeof(CkHeader)) return fail(ctx, RTLFS_E_ARG, "checkpoint buffer too small");
+    int rc = build_faults(ctx);
+    if (rc != RTLFS_OK) return rc;
+    CkHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, CK_MAGIC, 8) != 0) return fail(ctx, RTLFS_E_ARG, "not a checkpoint");
+    const uint64_t F = h.F, nd = h.n_designs;
+    if (h.W == 0 || h.window == 0 || h.n_live > F || h.n_carry > F || h.nodrop > 1 || nd > 65535)
+        return fail(ctx, RTLFS_E_ARG, "malformed checkpoint header");
+    // sizes the header implies, then the byte count must agree exactly
+    rtlfs_ctx::Checkpoint c;
+    c.T.resize(nd); c.n_net.resize(nd); c.det.resize(F); c.cycle.resize(F); c.port.resize(F);
+    c.load.resize(F); c.mism.resize(F); c.st_nreg.resize(F); c.st_r.resize(F * LIGHT_KR);
+    c.st_v.resize(F * LIGHT_KR); c.live.resize(h.n_live); c.carry.resize(h.n_carry);
+    c.pool_r.resize(h.pool_top); c.pool_v.resize(h.pool_top); c.heads.resize(8); c.rows.resize(h.n_rows);
+    uint64_t need = sizeof(CkHeader);
+    ck_fields(c, [&](auto &v) { need += v.size() * sizeof(v[0]); });
+    if (need != bytes) return fail(ctx, RTLFS_E_ARG, "checkpoint size does not match its header");
+    const unsigned char *p = static_cast<const unsigned char *>(buf) + sizeof(CkHeader);
+    ck_fields(c, [&](auto &v) {
+        if (!v.empty()) memcpy(v.data(), p, v.size() * sizeof(v[0]));
+        p += v.size() * sizeof(v[0]);
+    });
+    uint64_t rows = 0;
+    for (uint32_t n : c.n_net) rows += n;
+    if (rows != h.n_rows) return fail(ctx, RTLFS_E_ARG, "checkpoint rows do not match its designs");
+    for (uint32_t f : c.live) if (f >= F) return fail(ctx, RTLFS_E_ARG, "checkpoint names a fault out of range");
+    for (const HeavyCarry &x : c.carry)
+        if (x.fault >= F || x.off + x.nreg > h.pool_top) return fail(ctx, RTLFS_E_ARG, "checkpoint carry out of range");
+    c.window = h.window; c.W = h.W; c.F = h.F; c.nodrop = h.nodrop; c.valid = true;
+    rc = checkpoint_matches(ctx, c, c.W, c.nodrop != 0);
+    if (rc != RTLFS_OK) return rc;
+    ctx->ck = std::move(c);
+    ctx->err.clear();
+    return RTLFS_OK;
+}
 }  // extern "C"

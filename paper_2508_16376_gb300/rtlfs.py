@@ -43,8 +43,9 @@ class rtlfs_run_opts(ctypes.Structure):
                 ("heavy_frac", ctypes.c_float), ("use_graph", ctypes.c_int32),
                 ("fault_budget", ctypes.c_uint64), ("light_cap", ctypes.c_int32),
                 ("window", ctypes.c_int32), ("no_drop", ctypes.c_int32),
+                ("stop_cycle", ctypes.c_int32), ("resume", ctypes.c_int32),
                 ("heavy_form", ctypes.c_int32), ("good_cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("reserved", ctypes.c_uint32 * 1)]
 
 
 class rtlfs_stats(ctypes.Structure):
@@ -93,7 +94,11 @@ EXPORTS = {
     "rtlfs_mlp_train": ([V, V, V, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                          ctypes.c_float, V], ctypes.c_int),
     "rtlfs_fault_sim_static": ([V, ctypes.c_uint32, V, ctypes.c_uint32, V, V], ctypes.c_int),
+    "rtlfs_checkpoint_size": ([V, V], ctypes.c_int),
+    "rtlfs_checkpoint_save": ([V, V, ctypes.c_uint64], ctypes.c_int),
+    "rtlfs_checkpoint_load": ([V, V, ctypes.c_uint64], ctypes.c_int),
 }
+RTLFS_PENDING = 254
 MLP_PARAMS = 4609
 MLP_IN = 5
 
@@ -212,6 +217,24 @@ def rtlfs_mismatch_counts(ctx, design_id: int, n_faults: int) -> np.ndarray:
     out = np.zeros(max(n_faults, 0), np.uint32)
     _check(ctx, load_library().rtlfs_mismatch_counts(ctx, design_id, _ptr(out)))
     return out
+
+
+def rtlfs_checkpoint_size(ctx) -> int:
+    n = ctypes.c_uint64()
+    _check(ctx, load_library().rtlfs_checkpoint_size(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def rtlfs_checkpoint_save(ctx) -> bytes:
+    """The checkpoint held by the context (after a run with stop_cycle) as bytes."""
+    buf = np.zeros(rtlfs_checkpoint_size(ctx), np.uint8)
+    _check(ctx, load_library().rtlfs_checkpoint_save(ctx, _ptr(buf), buf.size))
+    return buf.tobytes()
+
+
+def rtlfs_checkpoint_load(ctx, data: bytes) -> None:
+    buf = np.frombuffer(data, np.uint8)
+    _check(ctx, load_library().rtlfs_checkpoint_load(ctx, _ptr(buf), buf.size))
 
 
 def _set_any_faults(ctx, did: int, faults) -> None:
@@ -376,6 +399,12 @@ class Simulator:
     def mismatch_counts(self, did: int) -> np.ndarray:
         """Per fault: cycles with a differing output in the last no-drop run."""
         return rtlfs_mismatch_counts(self.ctx, did, self.n_faults[did])
+
+    def checkpoint(self) -> bytes:
+        return rtlfs_checkpoint_save(self.ctx)
+
+    def restore(self, data: bytes) -> None:
+        rtlfs_checkpoint_load(self.ctx, data)
 
     def run(self, want_load: bool = False, **opts):
         o = make_opts(**opts) if opts else None
