@@ -129,6 +129,10 @@ struct rtlfs_ctx {
     DBuf<HeavyCarry> w_carry0, w_carry1;
     uint64_t w_pool_cap = 0;
     cudaEvent_t ev_wg = nullptr, ev_wl = nullptr;
+    // the good-trace launch lists of one span of cycles run side by side: the first on the
+    // caller's stream, the others on these, joined back through the events
+    cudaStream_t s_gaux[5] = {};
+    cudaEvent_t ev_gfork = nullptr, ev_gjoin[5] = {};
     std::vector<cudaEvent_t> ev_win;   // [4][nw]: light start/end, heavy start/end
     cudaEvent_t ev[8] = {};
     DBuf<DevDesign> d_designs;
@@ -146,7 +150,7 @@ struct rtlfs_ctx {
     DBuf<uint32_t> d_order;
     DBuf<HeavyItem> d_init_items, d_prom_items;
     DBuf<uint32_t> d_counters;        // [0] init count, [1] prom count
-    DBuf<uint32_t> d_err;             // set by a kernel whose bounded wait ran out
+    DBuf<uint32_t> d_err;             // bit 1: the heavy register-diff pool overflowed
     DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget,
                                       // [4..5] light evals/cycles, [6..7] heavy evals/cycles
     DBuf<HeavyVal> h_fval;
@@ -640,16 +644,6 @@ int prepare_good(rtlfs_ctx *ctx) {
         g.n_cl[lc] = (uint32_t)l_cl[lc].size();
     }
     if (good_smem_bytes(false, 0, 0, g.max_ch_g) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
-    for (uint32_t i : l_smem) {   // chunk instances of one good-trace launch fit 32 bits
-        const Design *D = ctx->designs[i];
-        if ((uint64_t)D->T * D->chunks.size() >= (1ull << 32))
-            return fail(ctx, RTLFS_E_ARG, "cycles x chunks too large for one launch: use windows");
-    }
-    for (uint32_t i : l_glob) {
-        const Design *D = ctx->designs[i];
-        if ((uint64_t)D->T * D->chunks.size() >= (1ull << 32))
-            return fail(ctx, RTLFS_E_ARG, "cycles x chunks too large for one launch: use windows");
-    }
     CU(ctx->d_err.reserve(1));
     g.n_smem = (uint32_t)l_smem.size();
     g.n_glob = (uint32_t)l_glob.size();
@@ -657,27 +651,51 @@ int prepare_good(rtlfs_ctx *ctx) {
     return RTLFS_OK;
 }
 
-// Good-trace launches of cycles [t0, t1) for every list on `stream`; *n counts them.
+// Good-trace launches of cycles [t0, t1) for every list, ordered on `stream` (work enqueued
+// on it later waits for all of them); *n counts them. The lists of different forms run
+// concurrently: each design is a CTA or cluster of its own, independent of the others.
 int launch_good_lists(rtlfs_ctx *ctx, cudaStream_t stream, uint32_t t0, uint32_t t1, uint32_t *n) {
     const GoodLaunch &g = ctx->gl;
-    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
-                         g.max_ch_s, true, ctx->d_err.p, stream, t0, t1));
-    CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
-                         ctx->d_err.p, stream, t0, t1));
-    *n += (g.n_smem ? 1 : 0) + (g.n_glob ? 1 : 0);
+    int k = 0;   // launches so far; the first goes on `stream`, the rest on s_gaux[k - 1]
+    auto next_stream = [&](cudaStream_t *out) -> int {
+        if (k == 0) {
+            *out = stream;
+        } else {
+            if (k == 1) CU(cudaEventRecord(ctx->ev_gfork, stream));
+            CU(cudaStreamWaitEvent(ctx->s_gaux[k - 1], ctx->ev_gfork, 0));
+            *out = ctx->s_gaux[k - 1];
+        }
+        ++k;
+        return RTLFS_OK;
+    };
+    cudaStream_t st = nullptr;
+    if (g.n_smem) {
+        if (int r = next_stream(&st)) return r;
+        CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
+                             g.max_ch_s, true, st, t0, t1));
+    }
+    if (g.n_glob) {
+        if (int r = next_stream(&st)) return r;
+        CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
+                             st, t0, t1));
+    }
     for (int lc = 1; lc < 5; ++lc) {
         if (!g.n_cl[lc]) continue;
+        if (int r = next_stream(&st)) return r;
         CU(launch_good_cluster(ctx->d_designs.p, ctx->d_list_cl[lc].p, g.n_cl[lc], 1u << lc, g.smem_cl[lc],
-                               ctx->d_err.p, stream, t0, t1));
-        ++*n;
+                               st, t0, t1));
     }
+    for (int j = 1; j < k; ++j) {   // join
+        CU(cudaEventRecord(ctx->ev_gjoin[j - 1], ctx->s_gaux[j - 1]));
+        CU(cudaStreamWaitEvent(stream, ctx->ev_gjoin[j - 1], 0));
+    }
+    *n += (uint32_t)k;
     return RTLFS_OK;
 }
 
 // Enqueue good trace + transposes on s_main (stream work only; prepare_good first).
 int launch_good(rtlfs_ctx *ctx, uint32_t *n_launches = nullptr) {
     uint32_t n = 0;
-    CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
     int rc = launch_good_lists(ctx, ctx->s_main, 0, 0xFFFFFFFFu, &n);
     if (rc != RTLFS_OK) return rc;
     for (Design *D : ctx->designs) {
@@ -1023,6 +1041,9 @@ int rtlfs_create(rtlfs_ctx **out, int device) {
         int lo_prio = 0, hi_prio = 0;
         CU(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
         CU(cudaStreamCreateWithPriority(&ctx->s_good, cudaStreamNonBlocking, hi_prio));
+        for (auto &x : ctx->s_gaux) CU(cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, hi_prio));
+        CU(cudaEventCreateWithFlags(&ctx->ev_gfork, cudaEventDisableTiming));
+        for (auto &e : ctx->ev_gjoin) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&ctx->ev_wg, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&ctx->ev_wl, cudaEventDisableTiming));
         for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
@@ -1050,6 +1071,9 @@ void rtlfs_destroy(rtlfs_ctx *ctx) {
     for (auto &e : ctx->ev_win) if (e) cudaEventDestroy(e);
     if (ctx->ev_wg) cudaEventDestroy(ctx->ev_wg);
     if (ctx->ev_wl) cudaEventDestroy(ctx->ev_wl);
+    for (auto &x : ctx->s_gaux) if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
+    if (ctx->ev_gfork) cudaEventDestroy(ctx->ev_gfork);
+    for (auto &e : ctx->ev_gjoin) if (e) cudaEventDestroy(e);
     if (ctx->s_good) { cudaStreamSynchronize(ctx->s_good); cudaStreamDestroy(ctx->s_good); }
     if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
     if (ctx->s_heavy) cudaStreamDestroy(ctx->s_heavy);
@@ -1138,10 +1162,7 @@ static int run_good_only(rtlfs_ctx *ctx) {
         if (!D->has_stim) return fail(ctx, RTLFS_E_STATE, "a design has no stimulus");
     int rc = enqueue_good(ctx);
     if (rc != RTLFS_OK) return rc;
-    uint32_t err = 0;
-    CU(cudaMemcpyAsync(&err, ctx->d_err.p, sizeof(err), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
-    if (err) return fail(ctx, RTLFS_E_CUDA, "good-trace descriptor staging did not complete (bounded wait ran out)");
     for (Design *D : ctx->designs) D->trace_valid = true;
     return RTLFS_OK;
 }
@@ -1426,6 +1447,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         launches = 0;
         CU(cudaEventRecord(ev[0], ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_heads.p, 0, 8 * sizeof(unsigned long long), ctx->s_main));
+        CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
         if (nodrop && F) {   // results are written at first detection; the rest stay undetected
             CU(cudaMemsetAsync(ctx->d_mism.p, 0, (size_t)F * sizeof(uint32_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->d_det.p, 0, (size_t)F, ctx->s_main));
@@ -1529,8 +1551,6 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         const uint32_t kerr = *reinterpret_cast<const uint32_t *>(ctx->p_small + 12);
         if (kerr & 2u)
             return fail(ctx, RTLFS_E_NOMEM, "heavy register-diff pool overflowed; run with window = 0");
-        if (kerr)
-            return fail(ctx, RTLFS_E_CUDA, "good-trace descriptor staging did not complete (bounded wait ran out)");
     }
     const unsigned long long *heads = ctx->p_small;
     const uint32_t *cnts = reinterpret_cast<const uint32_t *>(ctx->p_small + 8);
@@ -1655,11 +1675,8 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out) {
         CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
         CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
     }
-    uint32_t gerr = 0;
-    CU(cudaMemcpyAsync(&gerr, ctx->d_err.p, sizeof(gerr), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaEventRecord(ev[5], ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
-    if (gerr) return fail(ctx, RTLFS_E_CUDA, "good-trace descriptor staging did not complete (bounded wait ran out)");
     for (Design *D : ctx->designs) D->trace_valid = true;
     rtlfs_stats &st = ctx->stats;
     st = rtlfs_stats{};

@@ -17,10 +17,8 @@ enum : uint32_t {
 
 constexpr uint32_t NO_PORT = 0xFFFFFFFFu;
 
-// Threads of the good-trace CTA = maximum nodes per good-trace chunk, and the number of
-// chunk descriptor buffers the CTA keeps in flight (TMA staging).
+// Threads of the good-trace CTA = maximum nodes per good-trace chunk.
 constexpr uint32_t GOOD_BLOCK = 512;
-constexpr int GOOD_NBUF = 3;
 
 // Node descriptor, 16 bytes: x/y/z = operand net ids (CONST: y:x = value), w = meta.
 // meta bits: [0,4) op, [8,15) width 1..64, [16,24) k = shift amount, slice offset or
@@ -224,7 +222,7 @@ size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32
 // resumes from the trace row of cycle t_begin-1.
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              uint32_t max_chunks, bool use_smem, uint32_t *err,
+                              uint32_t max_chunks, bool use_smem,
                               cudaStream_t stream, uint32_t t_begin = 0,
                               uint32_t t_end = 0xFFFFFFFFu);
 // Activation bitplane of every fault for cycles [t0, t1) (t0 a multiple of 64; t1 a
@@ -247,7 +245,7 @@ size_t good_cluster_smem_bytes(uint32_t own, uint32_t rown, uint32_t n_inputs, u
 int good_cluster_max_active(uint32_t C, size_t smem);
 // Good trace of the listed designs over cycles [t_begin, t_end), one cluster of C CTAs each.
 cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *design_list,
-                                uint32_t n_list, uint32_t C, size_t smem, uint32_t *err,
+                                uint32_t n_list, uint32_t C, size_t smem,
                                 cudaStream_t stream, uint32_t t_begin, uint32_t t_end);
 cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int cap, int block,
                          int grid, cudaStream_t stream);

@@ -85,44 +85,20 @@ __device__ __forceinline__ FaultSite load_fault(const DevFaults &f, uint32_t fid
 // Good-machine trace. One CTA per design walks the cycles; inside a cycle the nodes of
 // one topological level are independent and are spread over the threads, with a
 // barrier between levels. The node list is cut into chunks of at most GOOD_BLOCK nodes
-// that never straddle a level, so every thread owns at most one node per chunk. The
-// chunks' descriptors are staged into shared memory by TMA bulk copies (cp.async.bulk,
-// completion counted on an mbarrier per buffer), GOOD_NBUF chunks ahead of use and
-// wrapping into the next cycle, so no thread ever waits on a global descriptor load.
-// Net values of the current cycle live in shared memory when they fit (USE_SMEM) and are
-// streamed to the row-major trace rows[t][net]. A staging wait that exceeds its bound
-// sets *err and lets the kernel run to its end (the host then reports a CUDA error).
+// that never straddle a level, so every thread owns at most one node per chunk. Each
+// thread loads its node descriptors two chunks ahead of use (wrapping into the next
+// cycle), so no evaluation waits on a global load. Net values of the current cycle live
+// in shared memory when they fit (USE_SMEM) and are streamed to the row-major trace
+// rows[t][net].
 // ===================================================================================
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void tma_issue(uint64_t *mbar, void *dst, const void *src, uint32_t bytes) {
-    const uint32_t mb = smem_u32(mbar);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(mb) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
-    const uint32_t mb = smem_u32(mbar);
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 template <bool USE_SMEM>
 __global__ void __launch_bounds__(GOOD_BLOCK, 1)
 good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
-                  uint32_t max_net, uint32_t max_reg, uint32_t max_chunks, uint32_t *err,
-                  uint32_t t_begin, uint32_t t_end) {
+                  uint32_t max_net, uint32_t max_reg, uint32_t max_chunks, uint32_t t_begin, uint32_t t_end) {
     extern __shared__ __align__(128) uint64_t gsm[];
     const DevDesign &D = designs[list[blockIdx.x]];
     const uint32_t I = D.I, R = D.R, IR = I + R, n_net = D.n_net, NC = D.n_chunks;
@@ -132,15 +108,9 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
     const size_t vwords = USE_SMEM ? (size_t)max_net + max_reg : 0;   // u64 words of values
     uint64_t *val = gsm;                                     // [max_net] when USE_SMEM
     uint64_t *qn = gsm + (USE_SMEM ? max_net : 0);           // [max_reg] when USE_SMEM
-    uint4 *stage = reinterpret_cast<uint4 *>(gsm + ((vwords + 15) & ~(size_t)15));   // [NBUF][GOOD_BLOCK]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(stage + GOOD_NBUF * GOOD_BLOCK);  // [NBUF]
-    uint2 *ch = reinterpret_cast<uint2 *>(mbar + GOOD_NBUF);                        // [max_chunks]
+    uint2 *ch = reinterpret_cast<uint2 *>(gsm + vwords);     // [max_chunks]
+    (void)max_chunks;
     for (uint32_t c = tid; c < NC; c += B) ch[c] = D.chunks[c];
-    if (tid == 0) {
-        for (int b = 0; b < GOOD_NBUF; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + b)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     // this thread's input and its first two registers, kept in registers for every cycle
     const uint64_t in_mask = tid < I ? wmask(D.net_w[tid]) : 0ull;
     const uint32_t r0 = tid, r1 = tid + B;
@@ -152,21 +122,20 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
     }
     __syncthreads();
 
-    // chunk instances of this launch (the host keeps windows small enough for 32 bits)
-    const uint32_t total = (T - t_begin) * NC;
-    uint32_t cf = 0;                           // chunk index of the next issue (wraps)
-    auto issue = [&](uint32_t buf) {           // thread 0: the next chunk instance into buf
+    // Each thread prefetches its node descriptor two chunks ahead into registers (coalesced
+    // loads from the L2-resident op graph, wrapping into the next cycle), so no evaluation
+    // waits on a global load; chunks of one level are independent, so only a chunk that
+    // ends a level is followed by a barrier.
+    uint32_t cf = 0;                           // chunk of the next prefetch (wraps)
+    auto prefetch = [&]() -> uint4 {
         const uint2 b = ch[cf];
-        const uint32_t n = (b.y & 0x7FFFFFFFu) - b.x;
-        tma_issue(mbar + buf, stage + buf * GOOD_BLOCK, D.desc + b.x, n * 16u);
+        const uint32_t n = b.x + tid;
         cf = cf + 1 == NC ? 0 : cf + 1;
+        return n < (b.y & 0x7FFFFFFFu) ? __ldg(D.desc + n) : make_uint4(0u, 0u, 0u, 0u);
     };
-    if (tid == 0)
-        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && k < total; ++k) issue(k);
-    uint32_t kc = 0;                           // chunk instance being consumed
-    uint32_t buf = 0, par = 0;                 // its buffer and the parity of that buffer's phase
+    uint4 dq0 = prefetch();
+    uint4 dq1 = prefetch();
     uint64_t s_next = (tid < I) ? __ldg(D.stim + (size_t)t_begin * I + tid) : 0ull;
-    bool failed = false;
 
     for (uint32_t t = t_begin; t < T; ++t) {
         uint64_t *row = D.rows + (size_t)t * n_net;
@@ -182,13 +151,13 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
             row[i] = v;
         }
         __syncthreads();
-        for (uint32_t c = 0; c < NC; ++c, ++kc) {
+        for (uint32_t c = 0; c < NC; ++c) {
             const uint2 b = ch[c];
             const uint32_t n = b.x + tid;
-            const bool mine = n < (b.y & 0x7FFFFFFFu);   // thread 0 always owns a node
-            const bool staged = mine ? mbar_wait(mbar + buf, par) : true;
-            if (staged && mine) {
-                const uint4 d0 = stage[buf * GOOD_BLOCK + tid];
+            const uint4 d0 = dq0;
+            dq0 = dq1;
+            dq1 = prefetch();
+            if (n < (b.y & 0x7FFFFFFFu)) {
                 const uint32_t op = meta_op(d0.w);
                 const int no = n_operands(op);
                 uint64_t a = 0, bb = 0, cc = 0;
@@ -199,27 +168,14 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
                 if (USE_SMEM) val[IR + n] = v;
                 row[IR + n] = v;
             }
-            // every thread is done with this buffer (and every wait succeeded): refill it
-            if (!__syncthreads_and(staged)) { failed = true; break; }
-            if (tid == 0 && kc + GOOD_NBUF < total) issue(buf);
-            if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
+            if (b.y & 0x80000000u) __syncthreads();   // the level's values are complete
         }
-        if (failed) break;
         if (USE_SMEM) {
             if (r0 < R) qn[r0] = val[rd0] & rm0;
             if (r1 < R) qn[r1] = val[rd1] & rm1;
             for (uint32_t r = tid + 2 * B; r < R; r += B) qn[r] = val[D.reg_d[r]] & wmask(D.net_w[I + r]);
         }
         __syncthreads();
-    }
-    if (failed && tid == 0) {
-        // a staging wait ran out: report it, give the copies still in flight a bounded
-        // chance to land, and leave
-        atomicOr(err, 1u);
-        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && kc + k < total; ++k) {
-            mbar_wait(mbar + buf, par);
-            if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
-        }
     }
 }
 
@@ -233,9 +189,9 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
 // (t+1)&1 while other registers' latches may still read Q_t from bank t&1 (a register
 // fed by a register). Every CTA keeps its own copy of the inputs. A cluster barrier
 // (release/acquire, so a level's values are visible cluster-wide) ends every level and
-// the latch. Each CTA streams its own descriptor list through shared memory by TMA as in
-// the single-CTA kernel; a level in which a CTA owns no node is an empty chunk that only
-// advances the buffer ring and joins the barrier.
+// the latch. Each CTA prefetches its own descriptor list two chunks ahead into registers
+// as in the single-CTA kernel; a level in which a CTA owns no node is an empty chunk that
+// only joins the barrier.
 // ===================================================================================
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -265,7 +221,7 @@ __device__ __forceinline__ uint64_t dsm_load(uint32_t local_addr, uint32_t rank)
 
 __global__ void __launch_bounds__(GOOD_BLOCK, 1)
 good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
-                    uint32_t *err, uint32_t t_begin, uint32_t t_end) {
+                    uint32_t t_begin, uint32_t t_end) {
     extern __shared__ __align__(128) uint64_t gsm[];
     const uint32_t rank = cluster_rank(), C = cluster_ctas();
     const DevDesign &D = designs[list[blockIdx.x / C]];
@@ -277,22 +233,13 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
     const size_t vwords = (size_t)own + 2 * (size_t)rown + I;
     uint64_t *qv = gsm + own;            // [2][rown] register banks (node values [own] before)
     uint64_t *inv = qv + 2 * rown;       // [I] inputs
-    uint4 *stage = reinterpret_cast<uint4 *>(gsm + ((vwords + 15) & ~(size_t)15));   // [NBUF][GOOD_BLOCK]
     const uint32_t c0 = D.cl_ch_off[rank], NC = D.cl_ch_off[rank + 1] - c0;
-    uint4 *ch = stage + GOOD_NBUF * GOOD_BLOCK;                                 // [NC]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(ch + NC);                     // [NBUF]
+    uint4 *ch = reinterpret_cast<uint4 *>(gsm + ((vwords + 1) & ~(size_t)1));   // [NC]
     const uint4 *__restrict__ cdesc = D.cl_desc + (size_t)rank * own;
     const uint4 *__restrict__ creg = D.cl_reg + D.cl_reg_off[rank];
     const uint32_t NR = D.cl_reg_off[rank + 1] - D.cl_reg_off[rank];
     const uint32_t base = smem_u32(gsm);
-    __shared__ uint32_t s_fail;   // a staging wait of this CTA ran out (set once, read after barriers)
-    if (tid == 0) s_fail = 0u;
     for (uint32_t c = tid; c < NC; c += B) ch[c] = D.cl_chunk[c0 + c];
-    if (tid == 0) {
-        for (int b = 0; b < GOOD_NBUF; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + b)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     // registers entering t_begin: the reset value, or the latch of the previous window
     for (uint32_t j = tid; j < NR; j += B) {
         const uint4 g = creg[j];
@@ -303,20 +250,14 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
     // all CTAs of the cluster are running and initialised before any remote read
     cluster_sync();
 
-    const uint32_t total = (T - t_begin) * NC;   // chunk instances (the host bounds it)
-    uint32_t cf = 0;
-    auto issue = [&](uint32_t buf) {             // thread 0: next chunk instance into buf
+    uint32_t cf = 0;                             // chunk of the next prefetch (wraps)
+    auto prefetch = [&]() -> uint4 {
         const uint4 b = ch[cf];
-        const uint32_t n = b.y & 0x7FFFFFFFu;
-        if (n) tma_issue(mbar + buf, stage + buf * GOOD_BLOCK, cdesc + b.x, n * 16u);
-        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(mbar + buf)) : "memory");
         cf = cf + 1 == NC ? 0 : cf + 1;
+        return tid < (b.y & 0x7FFFFFFFu) ? __ldg(cdesc + b.x + tid) : make_uint4(0u, 0u, 0u, 0u);
     };
-    if (tid == 0)
-        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && k < total; ++k) issue(k);
-    uint32_t kc = 0, buf = 0, par = 0;
-    bool failed = false;
-    uint32_t f_kc = 0, f_buf = 0, f_par = 0;     // where a staging wait ran out
+    uint4 dq0 = prefetch();
+    uint4 dq1 = prefetch();
 
     for (uint32_t t = t_begin; t < T; ++t) {
         uint64_t *row = D.rows + (size_t)t * n_net;
@@ -335,13 +276,12 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
             const uint32_t r = (e & CL_SELF) ? rank : ((e >> CL_RANK_SHIFT) & 15u);
             return dsm_load(base + w * 8u, r);
         };
-        for (uint32_t c = 0; c < NC; ++c, ++kc) {
+        for (uint32_t c = 0; c < NC; ++c) {
             const uint4 b = ch[c];
-            const uint32_t n = b.y & 0x7FFFFFFFu;
-            const bool mine = tid < n && !failed;
-            const bool staged = mine ? mbar_wait(mbar + buf, par) : true;
-            if (mine && staged) {
-                const uint4 d0 = stage[buf * GOOD_BLOCK + tid];
+            const uint4 d0 = dq0;
+            dq0 = dq1;
+            dq1 = prefetch();
+            if (tid < (b.y & 0x7FFFFFFFu)) {
                 const uint32_t op = meta_op(d0.w);
                 const int no = n_operands(op);
                 uint64_t a = 0, bb = 0, cc = 0;
@@ -352,36 +292,14 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
                 gsm[b.x + tid] = v;
                 row[IR + b.z + tid] = v;
             }
-            // every thread is done with this buffer (and every wait succeeded): refill it. At
-            // a level's end the cluster barrier (which completes the level cluster-wide) is
-            // that barrier too, with a failed wait reported through a shared flag.
-            bool all_staged;
-            if (b.y & 0x80000000u) {
-                if (!staged) s_fail = 1u;
-                cluster_sync();
-                all_staged = s_fail == 0u;
-            } else {
-                all_staged = __syncthreads_and(staged);
-            }
-            if (!all_staged && !failed) { failed = true; f_kc = kc; f_buf = buf; f_par = par; }
-            if (tid == 0 && !failed && kc + GOOD_NBUF < total) issue(buf);
-            if (++buf == (uint32_t)GOOD_NBUF) { buf = 0; par ^= 1u; }
+            if (b.y & 0x80000000u) cluster_sync();   // the level is complete cluster-wide
         }
         // latch: Q of cycle t+1 into the other bank
         for (uint32_t j = tid; j < NR; j += B) {
             const uint4 g = creg[j];
-            qv[(rown - bank_off) + j] = failed ? 0ull : (fetch(g.y) & wmask(g.z));
+            qv[(rown - bank_off) + j] = fetch(g.y) & wmask(g.z);
         }
         cluster_sync();
-    }
-    if (failed && tid == 0) {
-        // a staging wait ran out: report it and give the copies still in flight a bounded
-        // chance to land before the CTA exits
-        atomicOr(err, 1u);
-        for (uint32_t k = 0; k < (uint32_t)GOOD_NBUF && f_kc + k < total; ++k) {
-            mbar_wait(mbar + f_buf, f_par);
-            if (++f_buf == (uint32_t)GOOD_NBUF) { f_buf = 0; f_par ^= 1u; }
-        }
     }
 }
 
@@ -1823,13 +1741,12 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
 
 size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks) {
     const size_t vwords = use_smem ? (size_t)max_net + max_reg : 0;
-    return (((vwords + 15) & ~(size_t)15) * sizeof(uint64_t)) + (size_t)GOOD_NBUF * GOOD_BLOCK * 16 +
-           GOOD_NBUF * sizeof(uint64_t) + (size_t)max_chunks * sizeof(uint2);
+    return vwords * sizeof(uint64_t) + (size_t)max_chunks * sizeof(uint2);
 }
 
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              uint32_t max_chunks, bool use_smem, uint32_t *err, cudaStream_t stream,
+                              uint32_t max_chunks, bool use_smem, cudaStream_t stream,
                               uint32_t t_begin, uint32_t t_end) {
     if (n_list == 0) return cudaSuccess;
     const size_t smem = good_smem_bytes(use_smem, max_net, max_reg, max_chunks);
@@ -1839,22 +1756,21 @@ cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         good_trace_kernel<true><<<n_list, GOOD_BLOCK, smem, stream>>>(d_designs, design_list, max_net,
-                                                                     max_reg, max_chunks, err,
+                                                                     max_reg, max_chunks,
                                                                      t_begin, t_end);
     } else {
         e = cudaFuncSetAttribute(good_trace_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         good_trace_kernel<false><<<n_list, GOOD_BLOCK, smem, stream>>>(d_designs, design_list, 0, 0,
-                                                                      max_chunks, err, t_begin, t_end);
+                                                                      max_chunks, t_begin, t_end);
     }
     return cudaGetLastError();
 }
 
 size_t good_cluster_smem_bytes(uint32_t own, uint32_t rown, uint32_t n_inputs, uint32_t max_chunks) {
     const size_t vwords = (size_t)own + 2 * (size_t)rown + n_inputs;
-    return ((vwords + 15) & ~(size_t)15) * sizeof(uint64_t) + (size_t)GOOD_NBUF * GOOD_BLOCK * 16 +
-           (size_t)max_chunks * 16 + GOOD_NBUF * sizeof(uint64_t);
+    return ((vwords + 1) & ~(size_t)1) * sizeof(uint64_t) + (size_t)max_chunks * 16;
 }
 
 static cudaError_t good_cluster_attrs(uint32_t C, size_t smem) {
@@ -1886,7 +1802,7 @@ int good_cluster_max_active(uint32_t C, size_t smem) {
 }
 
 cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *design_list,
-                                uint32_t n_list, uint32_t C, size_t smem, uint32_t *err,
+                                uint32_t n_list, uint32_t C, size_t smem,
                                 cudaStream_t stream, uint32_t t_begin, uint32_t t_end) {
     if (n_list == 0) return cudaSuccess;
     cudaError_t e = good_cluster_attrs(C, smem);
@@ -1903,7 +1819,7 @@ cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *desi
     cfg.stream = stream;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, good_cluster_kernel, d_designs, design_list, err, t_begin, t_end);
+    return cudaLaunchKernelEx(&cfg, good_cluster_kernel, d_designs, design_list, t_begin, t_end);
 }
 
 cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,
