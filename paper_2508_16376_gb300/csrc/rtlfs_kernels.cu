@@ -128,6 +128,7 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
     // ends a level is followed by a barrier.
     uint32_t cf = 0;                           // chunk of the next prefetch (wraps)
     auto prefetch = [&]() -> uint4 {
+        if (NC == 0) return make_uint4(0u, 0u, 0u, 0u);   // a design without nodes
         const uint2 b = ch[cf];
         const uint32_t n = b.x + tid;
         cf = cf + 1 == NC ? 0 : cf + 1;
@@ -189,9 +190,10 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
 // (t+1)&1 while other registers' latches may still read Q_t from bank t&1 (a register
 // fed by a register). Every CTA keeps its own copy of the inputs. A cluster barrier
 // (release/acquire, so a level's values are visible cluster-wide) ends every level and
-// the latch. Each CTA prefetches its own descriptor list two chunks ahead into registers
-// as in the single-CTA kernel; a level in which a CTA owns no node is an empty chunk that
-// only joins the barrier.
+// the latch. Each CTA prefetches its own descriptor list three chunks ahead into
+// registers (one more than the single-CTA kernel: a remote operand read and the cluster
+// barrier make a level longer); a level in which a CTA owns no node is an empty chunk
+// that only joins the barrier.
 // ===================================================================================
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -252,12 +254,14 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
 
     uint32_t cf = 0;                             // chunk of the next prefetch (wraps)
     auto prefetch = [&]() -> uint4 {
+        if (NC == 0) return make_uint4(0u, 0u, 0u, 0u);   // a design without nodes
         const uint4 b = ch[cf];
         cf = cf + 1 == NC ? 0 : cf + 1;
         return tid < (b.y & 0x7FFFFFFFu) ? __ldg(cdesc + b.x + tid) : make_uint4(0u, 0u, 0u, 0u);
     };
     uint4 dq0 = prefetch();
     uint4 dq1 = prefetch();
+    uint4 dq2 = prefetch();
 
     for (uint32_t t = t_begin; t < T; ++t) {
         uint64_t *row = D.rows + (size_t)t * n_net;
@@ -280,7 +284,8 @@ good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__res
             const uint4 b = ch[c];
             const uint4 d0 = dq0;
             dq0 = dq1;
-            dq1 = prefetch();
+            dq1 = dq2;
+            dq2 = prefetch();
             if (tid < (b.y & 0x7FFFFFFFu)) {
                 const uint32_t op = meta_op(d0.w);
                 const int no = n_operands(op);
