@@ -170,7 +170,11 @@ typedef struct {
                                 shared memory, else one CTA over the global trace);
                                 1 = one CTA; 2, 4, 8 or 16 = clusters of that many CTAs
                                 (RTLFS_E_ARG when a design cannot run that way) */
-    uint32_t reserved[1];
+    int32_t  good_staging;   /* one-CTA good trace: 0 = each thread prefetches its node
+                                descriptors into registers two chunks ahead; 1 = a producer
+                                warp stages them into a shared-memory ring with bulk
+                                asynchronous copies (TMA) for the consumer threads. Same
+                                results; RTLFS_E_CUDA if a staging wait runs out */
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */

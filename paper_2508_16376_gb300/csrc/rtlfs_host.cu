@@ -138,6 +138,7 @@ struct rtlfs_ctx {
     DBuf<DevDesign> d_designs;
     DBuf<uint32_t> d_list_smem, d_list_glob, d_list_cl[5];
     uint32_t good_cluster = 0;         // good-trace mode of the next run (rtlfs_run_opts)
+    uint32_t good_staging = 0;         // one-CTA good trace through the staged (TMA) ring
     bool faults_dirty = true;
     uint32_t F = 0;
     std::vector<uint32_t> f_first;    // first global fault id of each design
@@ -150,7 +151,7 @@ struct rtlfs_ctx {
     DBuf<uint32_t> d_order;
     DBuf<HeavyItem> d_init_items, d_prom_items;
     DBuf<uint32_t> d_counters;        // [0] init count, [1] prom count
-    DBuf<uint32_t> d_err;             // bit 1: the heavy register-diff pool overflowed
+    DBuf<uint32_t> d_err;             // bit 0: a good-trace staging wait ran out; bit 1: the heavy pool overflowed
     DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget,
                                       // [4..5] light evals/cycles, [6..7] heavy evals/cycles
     DBuf<HeavyVal> h_fval;
@@ -607,7 +608,7 @@ int prepare_good(rtlfs_ctx *ctx) {
             // already on the shared-memory list (one launch covers the whole list)
             const uint32_t mn = std::max(g.max_net_s, D.n_net), mr = std::max(g.max_reg_s, D.R);
             const uint32_t mc = std::max(g.max_ch_s, nch);
-            if (good_smem_bytes(true, mn, mr, mc) <= SMEM_LIMIT) {
+            if (good_smem_bytes(true, mn, mr, mc, ctx->good_staging != 0) <= SMEM_LIMIT) {
                 l_smem.push_back((uint32_t)i);
                 g.max_net_s = mn; g.max_reg_s = mr; g.max_ch_s = mc;
             } else {
@@ -643,7 +644,8 @@ int prepare_good(rtlfs_ctx *ctx) {
         CU(ctx->d_list_cl[lc].upload(l_cl[lc]));
         g.n_cl[lc] = (uint32_t)l_cl[lc].size();
     }
-    if (good_smem_bytes(false, 0, 0, g.max_ch_g) > SMEM_LIMIT) return fail(ctx, RTLFS_E_ARG, "design has too many levels");
+    if (good_smem_bytes(false, 0, 0, g.max_ch_g, ctx->good_staging != 0) > SMEM_LIMIT)
+        return fail(ctx, RTLFS_E_ARG, "design has too many levels");
     CU(ctx->d_err.reserve(1));
     g.n_smem = (uint32_t)l_smem.size();
     g.n_glob = (uint32_t)l_glob.size();
@@ -672,12 +674,12 @@ int launch_good_lists(rtlfs_ctx *ctx, cudaStream_t stream, uint32_t t0, uint32_t
     if (g.n_smem) {
         if (int r = next_stream(&st)) return r;
         CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_smem.p, g.n_smem, g.max_net_s, g.max_reg_s,
-                             g.max_ch_s, true, st, t0, t1));
+                             g.max_ch_s, true, ctx->good_staging != 0, ctx->d_err.p, st, t0, t1));
     }
     if (g.n_glob) {
         if (int r = next_stream(&st)) return r;
         CU(launch_good_trace(ctx->d_designs.p, ctx->d_list_glob.p, g.n_glob, 0, 0, g.max_ch_g, false,
-                             st, t0, t1));
+                             ctx->good_staging != 0, ctx->d_err.p, st, t0, t1));
     }
     for (int lc = 1; lc < 5; ++lc) {
         if (!g.n_cl[lc]) continue;
@@ -696,6 +698,7 @@ int launch_good_lists(rtlfs_ctx *ctx, cudaStream_t stream, uint32_t t0, uint32_t
 // Enqueue good trace + transposes on s_main (stream work only; prepare_good first).
 int launch_good(rtlfs_ctx *ctx, uint32_t *n_launches = nullptr) {
     uint32_t n = 0;
+    CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
     int rc = launch_good_lists(ctx, ctx->s_main, 0, 0xFFFFFFFFu, &n);
     if (rc != RTLFS_OK) return rc;
     for (Design *D : ctx->designs) {
@@ -1162,7 +1165,10 @@ static int run_good_only(rtlfs_ctx *ctx) {
         if (!D->has_stim) return fail(ctx, RTLFS_E_STATE, "a design has no stimulus");
     int rc = enqueue_good(ctx);
     if (rc != RTLFS_OK) return rc;
+    uint32_t err = 0;
+    CU(cudaMemcpyAsync(&err, ctx->d_err.p, sizeof(err), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
+    if (err & 1u) return fail(ctx, RTLFS_E_CUDA, "good-trace staging did not complete (bounded wait ran out)");
     for (Design *D : ctx->designs) D->trace_valid = true;
     return RTLFS_OK;
 }
@@ -1187,6 +1193,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     if (o.good_cluster < 0 || o.good_cluster > (int)CL_MAX || (o.good_cluster > 1 && (o.good_cluster & (o.good_cluster - 1))))
         return fail(ctx, RTLFS_E_ARG, "good_cluster must be 0, 1, 2, 4, 8 or 16");
     ctx->good_cluster = (uint32_t)o.good_cluster;
+    if (o.good_staging < 0 || o.good_staging > 1) return fail(ctx, RTLFS_E_ARG, "good_staging must be 0 or 1");
+    ctx->good_staging = (uint32_t)o.good_staging;
     CU(cudaSetDevice(ctx->device));
     const auto t_host0 = std::chrono::steady_clock::now();
     int rc = build_faults(ctx);
@@ -1516,7 +1524,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
-                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv, (uint64_t)ctx->heavy_exact});
+                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv, (uint64_t)ctx->heavy_exact,
+                               (uint64_t)ctx->good_staging});
         for (int lc = 1; lc < 5; ++lc)
             key.insert(key.end(), {(uint64_t)g.n_cl[lc], (uint64_t)g.smem_cl[lc],
                                    (uint64_t)(uintptr_t)ctx->d_list_cl[lc].p});
@@ -1551,6 +1560,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         const uint32_t kerr = *reinterpret_cast<const uint32_t *>(ctx->p_small + 12);
         if (kerr & 2u)
             return fail(ctx, RTLFS_E_NOMEM, "heavy register-diff pool overflowed; run with window = 0");
+        if (kerr & 1u)
+            return fail(ctx, RTLFS_E_CUDA, "good-trace staging did not complete (bounded wait ran out)");
     }
     const unsigned long long *heads = ctx->p_small;
     const uint32_t *cnts = reinterpret_cast<const uint32_t *>(ctx->p_small + 8);
@@ -1675,8 +1686,11 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out) {
         CU(cudaMemcpyAsync(ctx->p_det, ctx->d_det.p, (size_t)F, cudaMemcpyDeviceToHost, ctx->s_main));
         CU(cudaMemcpyAsync(ctx->p_load, ctx->d_load.p, (size_t)F * 8, cudaMemcpyDeviceToHost, ctx->s_main));
     }
+    uint32_t gerr = 0;
+    CU(cudaMemcpyAsync(&gerr, ctx->d_err.p, sizeof(gerr), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaEventRecord(ev[5], ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
+    if (gerr & 1u) return fail(ctx, RTLFS_E_CUDA, "good-trace staging did not complete (bounded wait ran out)");
     for (Design *D : ctx->designs) D->trace_valid = true;
     rtlfs_stats &st = ctx->stats;
     st = rtlfs_stats{};

@@ -217,12 +217,12 @@ struct WinHeavy {
 };
 
 // Launchers (rtlfs_kernels.cu). All enqueue on `stream` and return the launch status.
-size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks);
+size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks, bool staged);
 // Good trace of cycles [t_begin, min(t_end, T)) of every listed design; t_begin > 0
 // resumes from the trace row of cycle t_begin-1.
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              uint32_t max_chunks, bool use_smem,
+                              uint32_t max_chunks, bool use_smem, bool staged, uint32_t *err,
                               cudaStream_t stream, uint32_t t_begin = 0,
                               uint32_t t_end = 0xFFFFFFFFu);
 // Activation bitplane of every fault for cycles [t0, t1) (t0 a multiple of 64; t1 a

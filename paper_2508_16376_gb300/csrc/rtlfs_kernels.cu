@@ -180,6 +180,178 @@ good_trace_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restr
     }
 }
 
+// Staged form of the single-CTA good trace: GOOD_BLOCK consumer threads plus one producer
+// warp. The producer copies each chunk's descriptors into a ring of GOOD_NSTAGE shared
+// buffers with bulk asynchronous copies (completion counted in bytes on the buffer's "full"
+// mbarrier); each consumer warp arrives on the buffer's "empty" mbarrier once its lanes have
+// read it, and the producer refills a buffer when every consumer warp has. Consumers
+// synchronise among themselves (named barrier 1) only where a level ends and around the
+// latch. Every wait is bounded: one that runs out sets a shared flag, after which no thread
+// waits on the ring again; the kernel then runs to its end without evaluating, waits (again
+// bounded) for copies still in flight, and reports through *err (bit 0).
+// ===================================================================================
+constexpr uint32_t GOOD_NSTAGE = 4;
+
+__device__ __forceinline__ void tma_issue(uint64_t *mbar, void *dst, const void *src, uint32_t bytes) {
+    const uint32_t mb = smem_u32(mbar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(mb) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    const uint32_t mb = smem_u32(mbar);
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" :: "n"(GOOD_BLOCK) : "memory");
+}
+
+template <bool USE_SMEM>
+__global__ void __launch_bounds__(GOOD_BLOCK + 32, 1)
+good_trace_staged_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
+                         uint32_t max_net, uint32_t max_reg, uint32_t max_chunks, uint32_t *err,
+                         uint32_t t_begin, uint32_t t_end) {
+    extern __shared__ __align__(128) uint64_t gsm[];
+    __shared__ __align__(8) uint64_t full[GOOD_NSTAGE], empty[GOOD_NSTAGE];
+    __shared__ uint32_t s_fail;                      // a bounded wait ran out
+    __shared__ unsigned long long s_issued;          // chunk instances the producer issued
+    const DevDesign &D = designs[list[blockIdx.x]];
+    const uint32_t I = D.I, R = D.R, IR = I + R, n_net = D.n_net, NC = D.n_chunks;
+    const uint32_t T = min(D.T, t_end);
+    if (t_begin >= T) return;   // the same for every thread of the CTA
+    const uint32_t tid = threadIdx.x, B = GOOD_BLOCK;
+    const size_t vwords = USE_SMEM ? (size_t)max_net + max_reg : 0;
+    uint64_t *val = gsm;
+    uint64_t *qn = gsm + (USE_SMEM ? max_net : 0);
+    uint4 *stage = reinterpret_cast<uint4 *>(gsm + ((vwords + 1) & ~(size_t)1));   // [NSTAGE][GOOD_BLOCK]
+    uint2 *ch = reinterpret_cast<uint2 *>(stage + GOOD_NSTAGE * GOOD_BLOCK);       // [max_chunks]
+    (void)max_chunks;
+    for (uint32_t c = tid; c < NC; c += blockDim.x) ch[c] = D.chunks[c];
+    if (tid == 0) {
+        s_fail = 0u;
+        s_issued = 0ull;
+        for (uint32_t b = 0; b < GOOD_NSTAGE; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(full + b)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(empty + b)), "n"(GOOD_BLOCK / 32) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const bool consumer = tid < B;
+    const uint64_t in_mask = consumer && tid < I ? wmask(D.net_w[tid]) : 0ull;
+    const uint32_t r0 = tid, r1 = tid + B;
+    const uint32_t rd0 = consumer && r0 < R ? D.reg_d[r0] : 0, rd1 = consumer && r1 < R ? D.reg_d[r1] : 0;
+    const uint64_t rm0 = consumer && r0 < R ? wmask(D.net_w[I + r0]) : 0, rm1 = consumer && r1 < R ? wmask(D.net_w[I + r1]) : 0;
+    if (USE_SMEM && consumer && t_begin > 0) {
+        const uint64_t *prev = D.rows + (size_t)(t_begin - 1) * n_net;
+        for (uint32_t r = tid; r < R; r += B) qn[r] = prev[D.reg_d[r]] & wmask(D.net_w[I + r]);
+    }
+    __syncthreads();
+    const unsigned long long total = (unsigned long long)(T - t_begin) * NC;
+
+    if (!consumer) {
+        // producer: one lane walks the chunk instances of the launch, wrapping over the list
+        if (tid == B) {
+            uint32_t cf = 0;
+            unsigned long long k = 0;
+            for (; k < total; ++k) {
+                const uint32_t b = (uint32_t)(k % GOOD_NSTAGE);
+                if (k >= GOOD_NSTAGE &&
+                    !mbar_wait(empty + b, (uint32_t)((k / GOOD_NSTAGE - 1) & 1ull))) {
+                    atomicExch(&s_fail, 1u);
+                    break;
+                }
+                if (*(volatile uint32_t *)&s_fail) break;
+                const uint2 c = ch[cf];
+                const uint32_t n = (c.y & 0x7FFFFFFFu) - c.x;   // >= 1: a chunk holds a node
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_issue(full + b, stage + b * GOOD_BLOCK, D.desc + c.x, n * 16u);
+                cf = cf + 1 == NC ? 0 : cf + 1;
+            }
+            s_issued = k;
+        }
+    } else {
+        const uint32_t lane = tid & 31u;
+        uint32_t kb = 0, kp = 0;                 // buffer and phase parity of the current instance
+        unsigned long long kc = 0;               // instances consumed
+        uint64_t s_next = tid < I ? __ldg(D.stim + (size_t)t_begin * I + tid) : 0ull;
+        for (uint32_t t = t_begin; t < T; ++t) {
+            uint64_t *row = D.rows + (size_t)t * n_net;
+            const uint64_t s_cur = s_next;
+            if (tid < I && t + 1 < T) s_next = __ldg(D.stim + (size_t)(t + 1) * I + tid);
+            for (uint32_t i = tid; i < IR; i += B) {
+                uint64_t v;
+                if (i < I) v = (i == tid ? s_cur : __ldg(D.stim + (size_t)t * I + i)) & (i == tid ? in_mask : wmask(D.net_w[i]));
+                else if (t == 0) v = 0ull;
+                else if (USE_SMEM) v = qn[i - I];
+                else v = (row - n_net)[D.reg_d[i - I]] & wmask(D.net_w[i]);
+                if (USE_SMEM) val[i] = v;
+                row[i] = v;
+            }
+            consumers_sync();
+            for (uint32_t c = 0; c < NC; ++c, ++kc) {
+                const uint2 b = ch[c];
+                const uint32_t n = b.x + tid;
+                // every consumer waits for the instance's copy, node or not: a warp that
+                // arrived on a buffer's "empty" barrier before its copy landed could run a
+                // whole ring ahead and arrive twice in one phase
+                const bool failed = *(volatile uint32_t *)&s_fail != 0u;
+                bool ok = false;
+                if (!failed) {
+                    ok = mbar_wait(full + kb, kp);
+                    if (!ok) atomicExch(&s_fail, 1u);
+                }
+                if (ok && n < (b.y & 0x7FFFFFFFu)) {
+                    {
+                        const uint4 d0 = stage[kb * GOOD_BLOCK + tid];
+                        const uint32_t op = meta_op(d0.w);
+                        const int no = n_operands(op);
+                        uint64_t a = 0, bb = 0, cc = 0;
+                        if (no >= 1) a = USE_SMEM ? val[d0.x] : row[d0.x];
+                        if (no >= 2) bb = USE_SMEM ? val[d0.y] : row[d0.y];
+                        if (no >= 3) cc = USE_SMEM ? val[d0.z] : row[d0.z];
+                        const uint64_t v = eval_op(d0, a, bb, cc);
+                        if (USE_SMEM) val[IR + n] = v;
+                        row[IR + n] = v;
+                    }
+                }
+                __syncwarp();   // this warp's lanes are done with the buffer
+                if (lane == 0 && !failed)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(empty + kb)) : "memory");
+                if (++kb == GOOD_NSTAGE) { kb = 0; kp ^= 1u; }
+                if (b.y & 0x80000000u) consumers_sync();   // the level's values are complete
+            }
+            if (USE_SMEM) {
+                if (r0 < R) qn[r0] = val[rd0] & rm0;
+                if (r1 < R) qn[r1] = val[rd1] & rm1;
+                for (uint32_t r = tid + 2 * B; r < R; r += B) qn[r] = val[D.reg_d[r]] & wmask(D.net_w[I + r]);
+            }
+            consumers_sync();
+        }
+        (void)kc;
+    }
+    __syncthreads();
+    if (s_fail && tid == 0) {
+        // report, and let copies still in flight land before the CTA's memory goes away: the
+        // instances after the last one whose buffer was waited on completely (at most the
+        // ring's depth)
+        atomicOr(err, 1u);
+        const unsigned long long issued = s_issued;
+        const unsigned long long from = issued > GOOD_NSTAGE ? issued - GOOD_NSTAGE : 0ull;
+        for (unsigned long long k = from; k < issued; ++k)
+            mbar_wait(full + (uint32_t)(k % GOOD_NSTAGE), (uint32_t)((k / GOOD_NSTAGE) & 1ull));
+    }
+}
+
 // ===================================================================================
 // Good-machine trace of a design too large for one CTA's shared memory: one cluster of
 // C CTAs (2..16) per design. Each CTA owns a contiguous share of every level's nodes and
@@ -1744,18 +1916,30 @@ plain_kernel(const DevDesign *__restrict__ designs, uint32_t design, DevFaults f
 
 // ---- launchers -----------------------------------------------------------------------
 
-size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks) {
+size_t good_smem_bytes(bool use_smem, uint32_t max_net, uint32_t max_reg, uint32_t max_chunks, bool staged) {
     const size_t vwords = use_smem ? (size_t)max_net + max_reg : 0;
+    if (staged)
+        return ((vwords + 1) & ~(size_t)1) * sizeof(uint64_t) + (size_t)GOOD_NSTAGE * GOOD_BLOCK * 16 +
+               (size_t)max_chunks * sizeof(uint2);
     return vwords * sizeof(uint64_t) + (size_t)max_chunks * sizeof(uint2);
 }
 
 cudaError_t launch_good_trace(const DevDesign *d_designs, const uint32_t *design_list,
                               uint32_t n_list, uint32_t max_net, uint32_t max_reg,
-                              uint32_t max_chunks, bool use_smem, cudaStream_t stream,
-                              uint32_t t_begin, uint32_t t_end) {
+                              uint32_t max_chunks, bool use_smem, bool staged, uint32_t *err,
+                              cudaStream_t stream, uint32_t t_begin, uint32_t t_end) {
     if (n_list == 0) return cudaSuccess;
-    const size_t smem = good_smem_bytes(use_smem, max_net, max_reg, max_chunks);
+    const size_t smem = good_smem_bytes(use_smem, max_net, max_reg, max_chunks, staged);
     cudaError_t e;
+    if (staged) {
+        const void *fn = use_smem ? (const void *)good_trace_staged_kernel<true> : (const void *)good_trace_staged_kernel<false>;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (!use_smem) max_net = max_reg = 0;
+        void *args[] = {(void *)&d_designs, (void *)&design_list, (void *)&max_net, (void *)&max_reg,
+                        (void *)&max_chunks, (void *)&err, (void *)&t_begin, (void *)&t_end};
+        return cudaLaunchKernel(fn, dim3(n_list), dim3(GOOD_BLOCK + 32), args, smem, stream);
+    }
     if (use_smem) {
         e = cudaFuncSetAttribute(good_trace_kernel<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -128,3 +128,27 @@ def test_forced_cluster_size_errors():
             with pytest.raises(RtlfsError):
                 sim.run(good_cluster=bad)
         sim.run(good_cluster=2)   # the context stays usable
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(window=64), dict(window=7), dict(use_graph=1)])
+@pytest.mark.parametrize("which", ["tiny", "fsm", "chain", "big"])
+def test_staged_good_trace(which, opts):
+    """The staged one-CTA good trace (a producer warp copying each chunk's descriptors into
+    a shared ring with bulk asynchronous copies) gives the oracle's trace and results: a
+    design without nodes (no chunks at all), windows that resume mid-stimulus and end on a
+    ragged cycle, graph replay, and a design whose net values only fit one CTA's shared
+    memory without the ring (then on a cluster as before)."""
+    _check(which, good_staging=1, **opts)
+
+
+def test_staged_and_prefetched_forms_alternate():
+    """Switching between the register-prefetched and the staged one-CTA trace on one
+    context keeps the trace and the results."""
+    d, stim, f, trace, exp = _case("fsm300")
+    with Simulator(0) as sim:
+        sim.add(d, stim, f)
+        for kw in (dict(good_staging=1), dict(), dict(good_staging=1, window=64), dict(window=64)):
+            res, _ = sim.run(**kw)
+            assert np.array_equal(sim.good_trace(0), trace), str(kw)
+            for a, b in zip(split(res[0]), exp):
+                assert np.array_equal(a, b), str(kw)

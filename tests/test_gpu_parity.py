@@ -293,6 +293,9 @@ def test_error_codes():
         # the context stays usable after the rejected calls
         rtlfs.rtlfs_set_stimulus(ctx, did, synth.stimulus(good, 30, 1))
         rtlfs.rtlfs_set_faults(ctx, did, rtlfs.fault_array(synth.sample_faults(good, 50, 1)))
+        with pytest.raises(rtlfs.RtlfsError) as e:
+            rtlfs.rtlfs_run(ctx, [50], rtlfs.make_opts(good_staging=2))
+        assert e.value.code == rtlfs.RTLFS_E_ARG
         res, _, _ = rtlfs.rtlfs_run(ctx, [50])
         assert len(res[0]) == 50
     finally:
