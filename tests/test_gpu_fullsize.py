@@ -1,4 +1,5 @@
-"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times (its own
+workload and options, imported from it), for each fault list and mode it can time.
 
 The oracle cannot finish 100k faults x 10k cycles of the medium design in a test, so it
 checks a stratified sample fault by fault -- the highest propagation loads, the latest
@@ -12,6 +13,7 @@ import os
 import numpy as np
 import pytest
 
+import bench
 import oracle
 from paper_2508_16376_gb300 import rtlfs, synth
 from paper_2508_16376_gb300.rtlfs import Simulator, split
@@ -42,18 +44,71 @@ def _stratified(res, loads, faults, design, k, seed):
 
 
 def test_medium_full_size():
-    """The bench workload: 20k nodes, 10k cycles, 100k faults, default options."""
-    d, stim, f = synth.workload("medium")
+    """The bench workload (20k nodes, 10k cycles, 100k faults) in the launch configuration
+    the bench times (windows of 256 cycles, light capacity 1) and in the one-pass form."""
+    d, stim, f = bench.workload(0)
     with Simulator(0) as sim:
         sim.add(d, stim, f)
-        res, loads = sim.run(want_load=True)
+        res, loads = sim.run(want_load=True, **bench.DEFAULT_OPTS)
+        res1, loads1 = sim.run(want_load=True)
         plain = sim.run_plain()
-    for a, b in zip(split(res[0]), split(plain[0])):
-        assert np.array_equal(a, b)
+    for a, b, c in zip(split(res[0]), split(plain[0]), split(res1[0])):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.array_equal(loads[0], loads1[0])
     idx = _stratified(res[0], loads[0], f, d, 12, 1)
     exp = oracle.fault_sim(d, stim, f.take(idx), threads=os.cpu_count() or 4)
     for a, b in zip(split(res[0][idx]), exp):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("model", ["transient", "mixed"])
+def test_medium_full_size_fault_models(model):
+    """The bench's other fault lists at full size (100k transient faults; stuck-at plus every
+    output-port fault plus transient faults): every fault against the plain GPU form, a
+    stratified sample against the oracle."""
+    d, stim, f = bench.workload(0, 0, model)
+    with Simulator(0) as sim:
+        sim.add(d, stim, f)
+        res, loads = sim.run(want_load=True, **bench.DEFAULT_OPTS)
+        plain = sim.run_plain()
+    for a, b in zip(split(res[0]), split(plain[0])):
+        assert np.array_equal(a, b)
+    idx = _stratified(res[0], loads[0], f, d, 8, 3)
+    exp = oracle.fault_sim(d, stim, f.take(idx), threads=os.cpu_count() or 4)
+    for a, b in zip(split(res[0][idx]), exp):
+        assert np.array_equal(a, b)
+
+
+def test_medium_full_size_no_drop():
+    """The no-drop mode at full size (every fault to the last cycle): first detections and
+    mismatch-cycle counts of a stratified sample against the oracle's no-drop run."""
+    d, stim, f = bench.workload(0, 0, "mixed")
+    with Simulator(0) as sim:
+        sim.add(d, stim, f)
+        res, loads = sim.run(want_load=True, no_drop=1, **bench.DEFAULT_OPTS)
+        cnt = sim.mismatch_counts(0)
+    idx = _stratified(res[0], loads[0], f, d, 6, 4)
+    exp = oracle.fault_sim_ex(d, stim, f.take(idx), threads=os.cpu_count() or 4, no_drop=True)
+    for a, b in zip(split(res[0][idx]), exp[:3]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(cnt[idx], exp[3])
+
+
+def test_medium_full_size_checkpoint():
+    """A full-size campaign stopped at cycle 5120, saved, loaded into a fresh context and
+    resumed equals the uninterrupted campaign (results and loads)."""
+    d, stim, f = bench.workload(0)
+    with Simulator(0) as sim:
+        sim.add(d, stim, f)
+        ref, ref_loads = sim.run(want_load=True, **bench.DEFAULT_OPTS)
+        sim.run(stop_cycle=5120, **bench.DEFAULT_OPTS)
+        blob = sim.checkpoint()
+    with Simulator(0) as sim:
+        sim.add(d, stim, f)
+        sim.restore(blob)
+        res, loads = sim.run(want_load=True, resume=1, **bench.DEFAULT_OPTS)
+    assert np.array_equal(res[0], ref[0])
+    assert np.array_equal(loads[0], ref_loads[0])
 
 
 def test_large_design_subsample():
