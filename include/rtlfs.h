@@ -163,7 +163,10 @@ typedef struct {
                                 exact one unless it costs resident CTAs), 1 = a shared-memory
                                 bit per net, 2 = a small shared filter plus cycle stamps on
                                 the values in global scratch (for designs whose per-net
-                                bitmap would crowd shared memory) */
+                                bitmap would crowd shared memory), 3 = as 2 with the
+                                per-node bitmap in global scratch too and a one-bit-per-word
+                                summary in shared memory (for designs whose node bitmap
+                                would crowd it; heavy_block 32 only) */
     int32_t  good_cluster;   /* good-trace form: 0 = auto (one CTA with the net values in
                                 shared memory when the design fits, else the smallest
                                 thread-block cluster whose CTAs hold them in distributed

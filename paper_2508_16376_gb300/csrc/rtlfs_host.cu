@@ -160,6 +160,8 @@ struct rtlfs_ctx {
     DBuf<uint64_t> h_regv;
     uint32_t heavy_slots = 0, heavy_grid = 0, hs_net = 0, hs_reg = 0, hs_node = 0, hs_lv = 0;
     bool heavy_exact = false;          // the heavy kernel's form for the current designs
+    bool heavy_gbm = false;            // node bitmaps in global scratch (h_gbm)
+    DBuf<uint32_t> h_gbm;
     bool stamps_stale = false;         // the exact form wrote values over stamp fields since
                                        // the scratch was last zeroed
     // scheduler state
@@ -777,15 +779,28 @@ int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots, int form) {
         mn = std::max(mn, D->n_net); mr = std::max(mr, D->R);
         mnode = std::max(mnode, D->N); ml = std::max(ml, D->n_levels);
     }
-    // the exact form (a shared bit per net) unless that bitmap costs resident CTAs
-    const size_t smem_s = heavy_smem_bytes(mnode, ml, mn, false), smem_x = heavy_smem_bytes(mnode, ml, mn, true);
-    if (smem_s > 220 * 1024) return fail(ctx, RTLFS_E_ARG, "design too large for the heavy kernel bitmap");
-    const int per_sm_s = heavy_max_blocks_per_sm(block, smem_s, false);
-    const int per_sm_x = smem_x <= 220 * 1024 ? heavy_max_blocks_per_sm(block, smem_x, true) : 0;
-    const bool exact = form == 1 ? per_sm_x > 0 : form == 2 ? false : per_sm_x >= per_sm_s;
-    const int per_sm = exact ? per_sm_x : per_sm_s;
+    // The exact form (a shared bit per net) unless that bitmap costs resident CTAs; the
+    // global-bitmap form (node bitmap in global scratch, one warp per fault) when the node
+    // bitmap in shared memory would halve the resident CTAs or worse: its marks and gathers
+    // go through L2, which costs more per level than the occupancy it buys below that.
+    if (form == 3 && block != 32) return fail(ctx, RTLFS_E_ARG, "heavy_form 3 needs heavy_block 32");
+    const size_t smem_s = heavy_smem_bytes(mnode, ml, mn, false, false), smem_x = heavy_smem_bytes(mnode, ml, mn, true, false);
+    const size_t smem_g = heavy_smem_bytes(mnode, ml, mn, false, true);
+    const int per_sm_s = smem_s <= 220 * 1024 ? heavy_max_blocks_per_sm(block, smem_s, false, false) : 0;
+    const int per_sm_x = smem_x <= 220 * 1024 ? heavy_max_blocks_per_sm(block, smem_x, true, false) : 0;
+    const int per_sm_g = block == 32 && smem_g <= 220 * 1024 ? heavy_max_blocks_per_sm(block, smem_g, false, true) : 0;
+    bool gbm = false, exact = false;
+    if (form == 1) exact = per_sm_x > 0;
+    else if (form == 3) gbm = true;
+    else if (form == 0) {
+        exact = per_sm_x >= per_sm_s;
+        gbm = per_sm_g >= 2 * std::max(per_sm_x, per_sm_s);
+        if (gbm) exact = false;
+    }
+    const int per_sm = gbm ? per_sm_g : exact ? per_sm_x : per_sm_s;
     if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "heavy kernel cannot be resident with block %d", block);
     ctx->heavy_exact = exact;
+    ctx->heavy_gbm = gbm;
     if (exact) {
         ctx->stamps_stale = true;   // its 8-byte values overwrite stamp fields
     }
@@ -803,6 +818,14 @@ int ensure_heavy_scratch(rtlfs_ctx *ctx, int block, int want_slots, int form) {
     }
     ctx->hs_node = mnode; ctx->hs_lv = ml;
     ctx->heavy_grid = (uint32_t)slots;
+    if (gbm) {   // node bitmaps start zero and every fault leaves them zero
+        const size_t need = (size_t)slots * ((mnode + 31) / 32);
+        if (ctx->h_gbm.n < need) {
+            ctx->h_gbm.release();
+            CU(ctx->h_gbm.reserve(need));
+            CU(cudaMemsetAsync(ctx->h_gbm.p, 0, ctx->h_gbm.n * sizeof(uint32_t), ctx->s_main));
+        }
+    }
     if (!exact && ctx->stamps_stale) {
         // stamp 0 is never current: zeroed entries and counters start every slot clean
         // (on the main stream, which every heavy launch of the campaign waits behind)
@@ -820,6 +843,7 @@ HeavyScratch heavy_view(rtlfs_ctx *ctx) {
     s.reg_r = ctx->h_regr.p; s.reg_v = ctx->h_regv.p;
     s.max_net = ctx->hs_net; s.max_reg = ctx->hs_reg; s.max_node = ctx->hs_node;
     s.exact = ctx->heavy_exact ? 1u : 0u;
+    s.gbm = ctx->heavy_gbm ? ctx->h_gbm.p : nullptr;
     s.max_levels = ctx->hs_lv;
     return s;
 }
@@ -1217,7 +1241,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         rc = ensure_sched_buffers(ctx);
         if (rc != RTLFS_OK) return rc;
     }
-    if (o.heavy_form < 0 || o.heavy_form > 2) return fail(ctx, RTLFS_E_ARG, "heavy_form must be 0, 1 or 2");
+    if (o.heavy_form < 0 || o.heavy_form > 3) return fail(ctx, RTLFS_E_ARG, "heavy_form must be 0, 1, 2 or 3");
     rc = ensure_heavy_scratch(ctx, hblock, o.heavy_ctas, o.heavy_form);
     if (rc != RTLFS_OK) return rc;
     rc = prepare_good(ctx);
@@ -1510,7 +1534,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                                      (uint64_t)lgrid, (uint64_t)hblock, (uint64_t)hgrid,
                                      (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W,
                                      (uint64_t)nodrop};
-        const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p,
+        const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p, ctx->h_gbm.p,
                               ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
                               ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,
                               ctx->d_bit.p, ctx->d_val.p, ctx->d_fdesign.p, ctx->p_cycle, ctx->p_port,
@@ -1524,7 +1548,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
-                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv, (uint64_t)ctx->heavy_exact,
+                               ctx->hs_net, ctx->hs_reg, ctx->hs_node, ctx->hs_lv, (uint64_t)ctx->heavy_exact, (uint64_t)ctx->heavy_gbm,
                                (uint64_t)ctx->good_staging});
         for (int lc = 1; lc < 5; ++lc)
             key.insert(key.end(), {(uint64_t)g.n_cl[lc], (uint64_t)g.smem_cl[lc],

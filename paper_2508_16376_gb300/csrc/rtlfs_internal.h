@@ -159,6 +159,7 @@ struct HeavyScratch {
     uint32_t *stamp;     // [slots] last stamp each slot used
     uint32_t *reg_r;     // [slots][2][max_reg]
     uint64_t *reg_v;     // [slots][2][max_reg]
+    uint32_t *gbm;       // global-bitmap form: [slots][(max_node + 31) / 32] node bitmaps (zeroed)
     uint32_t max_net, max_reg, max_node, max_levels;
     // 1: the exact form -- a shared-memory bit per net marks the faulty values (8-byte values
     // at the start of each slot's array); 0: the stamped form (a small shared filter and
@@ -251,13 +252,14 @@ cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int 
                          int grid, cudaStream_t stream);
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream);
-size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net, bool exact);
+// Dynamic shared memory of one heavy CTA (gbm: node bitmap in global scratch, a summary here).
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net, bool exact, bool gbm);
 cudaError_t launch_plain(const DevDesign *d_designs, uint32_t design, DevFaults f,
                          uint32_t first, uint32_t count, uint64_t *fval, uint32_t *stamp,
                          uint32_t *qstamp, uint32_t *heap, uint32_t *reg_r, uint64_t *reg_v,
                          uint32_t stride_net, uint32_t stride_node, uint32_t stride_reg,
                          cudaStream_t stream);
 int light_max_blocks_per_sm(int cap, int block);
-int heavy_max_blocks_per_sm(int block, size_t smem, bool exact);
+int heavy_max_blocks_per_sm(int block, size_t smem, bool exact, bool gbm);
 
 }  // namespace rtlfs

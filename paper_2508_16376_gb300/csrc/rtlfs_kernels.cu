@@ -597,34 +597,52 @@ struct HeavySmem {
     uint32_t *dlist;              // [HEAVY_DLIST]
     uint2 *frange;                // [HEAVY_FRANGE] fan-out ranges (8-byte aligned)
     unsigned long long *lvm;      // [nlw] one bit per level that has dirty nodes
-    uint32_t nwd, nlw;
+    // global-bitmap form: bm lives in the slot's global scratch and this shared summary has a
+    // bit per bitmap word that may hold a mark this cycle (cleared at the cycle's end)
+    uint32_t *top;                // [nwt]
+    uint32_t nwd, nlw, nwt;
 };
 
-template <bool EXACT>
-__device__ __forceinline__ HeavySmem heavy_layout(uint32_t *hsm, const HeavyScratch &S) {
+// Shared-memory words of the node record of one heavy CTA: the node bitmap itself, or, in
+// the global-bitmap form, its one-bit-per-word summary.
+__host__ __device__ inline size_t heavy_node_words(uint32_t max_node, bool gbm) {
+    const size_t nwn = (size_t)(max_node + 31) / 32;
+    return gbm ? (nwn + 31) / 32 : nwn;
+}
+
+template <bool EXACT, bool GBM = false>
+__device__ __forceinline__ HeavySmem heavy_layout(uint32_t *hsm, const HeavyScratch &S, uint32_t slot = 0) {
     HeavySmem m;
     const uint32_t nwn = (S.max_node + 31) / 32;
+    const size_t nodew = heavy_node_words(S.max_node, GBM);
     m.nwd = (S.max_net + 31) / 32;
     m.nlw = (S.max_levels + 63) / 64;
-    m.bm = hsm;
-    m.cnt = m.bm + nwn;
+    m.nwt = GBM ? (uint32_t)nodew : 0u;
+    m.bm = GBM ? S.gbm + (size_t)slot * nwn : hsm;
+    m.top = GBM ? hsm : nullptr;
+    m.cnt = hsm + nodew;
     m.nlist = m.cnt + S.max_levels;
     m.flt = m.nlist + HEAVY_NLIST;
     m.dbm = m.flt + (EXACT ? 0 : HEAVY_FILTER / 32);
     m.dlist = m.dbm + (EXACT ? m.nwd : 0);
     const size_t side = EXACT ? (size_t)m.nwd + HEAVY_DLIST : HEAVY_FILTER / 32;
-    const size_t fr_words = ((size_t)nwn + S.max_levels + HEAVY_NLIST + side + 1) & ~(size_t)1;
+    const size_t fr_words = (nodew + S.max_levels + HEAVY_NLIST + side + 1) & ~(size_t)1;
     m.frange = reinterpret_cast<uint2 *>(hsm + fr_words);
     m.lvm = reinterpret_cast<unsigned long long *>(m.frange + HEAVY_FRANGE);
     return m;
 }
 
-// Zero the bitmaps and counters once per CTA; every fault leaves them zero again.
-template <bool EXACT>
+// Zero the bitmaps and counters once per CTA; every fault leaves them zero again (the
+// global node bitmaps of the global-bitmap form are zeroed when allocated).
+template <bool EXACT, bool GBM = false>
 __device__ __forceinline__ void heavy_zero(const HeavySmem &m, const HeavyScratch &S, HeavyVars &V) {
     const uint32_t tid = threadIdx.x, B = blockDim.x;
     const uint32_t nwn = (S.max_node + 31) / 32;
-    for (uint32_t i = tid; i < nwn; i += B) m.bm[i] = 0;
+    if (GBM) {
+        for (uint32_t i = tid; i < m.nwt; i += B) m.top[i] = 0;
+    } else {
+        for (uint32_t i = tid; i < nwn; i += B) m.bm[i] = 0;
+    }
     for (uint32_t i = tid; i < S.max_levels; i += B) m.cnt[i] = 0;
     if (EXACT) {
         for (uint32_t i = tid; i < m.nwd; i += B) m.dbm[i] = 0;
@@ -965,7 +983,7 @@ __device__ __forceinline__ void heavy_run_fault(const DevDesign &D, const DevFau
 // prefix sum instead of shared atomics, the detecting port and the evaluation count kept
 // per lane and reduced once per cycle, and the level bitmap cleared once per cycle. Same
 // results and the same evaluation counts as heavy_run_fault.
-template <bool EXACT>
+template <bool EXACT, bool GBM>
 __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const DevFaults &f, uint32_t fid,
                                                      uint32_t tend, unsigned long long budget,
                                                      const HeavySmem &sm, HeavyVars &V, HeavyVal *fval, uint32_t &stamp,
@@ -1014,8 +1032,16 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
     };
     auto mark = [&](uint32_t c, uint32_t lv) {
         const uint32_t b1 = 1u << (c & 31u);
-        const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
-        if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
+        if (GBM) {
+            // a reduction on the global word (no value back) and its summary bit; the level's
+            // count may include a node marked twice, which only errs towards the scan path
+            atomicOr(&bm[c >> 5], b1);
+            atomicOr(&sm.top[c >> 10], 1u << ((c >> 5) & 31u));
+            if (atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
+        } else {
+            const uint32_t o2 = atomicOr(&bm[c >> 5], b1);
+            if (!(o2 & b1) && atomicAdd(&cnt[lv], 1u) == 0u) atomicOr(&lvm[lv >> 6], 1ull << (lv & 63u));
+        }
     };
     auto mark_range = [&](uint32_t e0, uint32_t e1, uint32_t first, uint32_t step) {
         for (uint32_t e = e0 + first; e < e1; e += step) mark(__ldg(fo_idx + e), __ldg(fo_lvl + e));
@@ -1191,6 +1217,7 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
             if (L >= NL) break;
             const uint32_t lo = __ldg(D.lvl_start + L), hi = __ldg(D.lvl_start + L + 1);
             const uint32_t w0 = lo >> 5, w1 = (hi - 1) >> 5;
+            if (GBM) __threadfence_block();   // the warp's global marks are visible to its loads
             if (cnt[L] <= HEAVY_NLIST) {
                 // gather: one bitmap word per lane, positions from a warp prefix sum; no
                 // marks happen meanwhile, so each lane clears its word's level bits plainly
@@ -1202,9 +1229,17 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
                         uint32_t wm = 0xFFFFFFFFu;
                         if (w == w0) wm &= 0xFFFFFFFFu << (lo & 31u);
                         if (w == w1 && (hi & 31u)) wm &= (1u << (hi & 31u)) - 1u;
-                        const uint32_t word = bm[w];
-                        bits = word & wm;
-                        if (bits) bm[w] = word & ~wm;
+                        if (GBM) {
+                            if ((sm.top[w >> 5] >> (w & 31u)) & 1u) {   // the word may hold marks
+                                const uint32_t word = __ldcg(bm + w);
+                                bits = word & wm;
+                                if (bits) __stcg(bm + w, word & ~wm);
+                            }
+                        } else {
+                            const uint32_t word = bm[w];
+                            bits = word & wm;
+                            if (bits) bm[w] = word & ~wm;
+                        }
                     }
                     const uint32_t cb = (uint32_t)__popc(bits);
                     uint32_t incl = cb;
@@ -1226,7 +1261,14 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
                     uint32_t wm = 0xFFFFFFFFu;
                     if (w == w0) wm &= 0xFFFFFFFFu << (lo & 31u);
                     if (w == w1 && (hi & 31u)) wm &= (1u << (hi & 31u)) - 1u;
-                    if (!(bm[w] & wm)) continue;
+                    if (GBM) {
+                        // evaluations of this level may mark the next level's nodes in the same
+                        // word meanwhile: clear this level's bits atomically
+                        if (!((sm.top[w >> 5] >> (w & 31u)) & 1u)) continue;
+                        if (!(__ldcg(bm + w) & wm)) continue;
+                    } else if (!(bm[w] & wm)) {
+                        continue;
+                    }
                     uint32_t bits = atomicAnd(&bm[w], ~wm) & wm;
                     for (; bits; bits &= bits - 1) eval_node((w << 5) + (uint32_t)(__ffs(bits) - 1));
                 }
@@ -1243,6 +1285,8 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
         const uint32_t minport = __reduce_min_sync(FULL, pmin);
         __syncwarp();
         for (uint32_t i = lane; i < nlw; i += 32) lvm[i] = 0;
+        if (GBM)   // every marked word was gathered and cleared; the summary bits may be stale
+            for (uint32_t i = lane; i < sm.nwt; i += 32) sm.top[i] = 0;
         if (EXACT) {   // clear the net bitmap for the next cycle
             const uint32_t nd = V.nd;
             if (nd <= HEAVY_DLIST) {
@@ -1275,20 +1319,20 @@ __device__ __forceinline__ void hsync() {
     if (WARP) __syncwarp(); else __syncthreads();
 }
 
-template <bool WARP, bool EXACT>
+template <bool WARP, bool EXACT, bool GBM = false>
 __global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_n_items;
-    const HeavySmem sm = heavy_layout<EXACT>(hsm, S);
     const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
+    const HeavySmem sm = heavy_layout<EXACT, GBM>(hsm, S, slot);
     HeavyVal *fval = S.fval + (size_t)slot * S.max_net;
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
     uint32_t stamp = EXACT ? 0u : S.stamp[slot];   // the same in every thread, advanced together
-    heavy_zero<EXACT>(sm, S, V);
+    heavy_zero<EXACT, GBM>(sm, S, V);
     hsync<WARP>();
 
     for (;;) {
@@ -1309,7 +1353,7 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
         if (tid == 0) V.load = 0;
         hsync<WARP>();
         HeavyRun r{it.t, it.nreg, 0, 0, -1, -1, 0};
-        if (WARP) heavy_run_fault_warp<EXACT>(D, f, fid, D.T, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
+        if (WARP) heavy_run_fault_warp<EXACT, GBM>(D, f, fid, D.T, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
         else heavy_run_fault<EXACT>(D, f, fid, D.T, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
         hsync<WARP>();
         if (tid == 0) {
@@ -1333,19 +1377,19 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
 // Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
 // from the last window and those promoted in this one; survivors carry their register
 // diffs to the next window through the pool.
-template <bool WARP, bool EXACT>
+template <bool WARP, bool EXACT, bool GBM = false>
 __global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
     __shared__ unsigned long long s_item, s_off;
-    const HeavySmem sm = heavy_layout<EXACT>(hsm, S);
     const uint32_t tid = threadIdx.x, B = blockDim.x, slot = blockIdx.x;
+    const HeavySmem sm = heavy_layout<EXACT, GBM>(hsm, S, slot);
     HeavyVal *fval = S.fval + (size_t)slot * S.max_net;
     uint32_t *regR = S.reg_r + (size_t)slot * 2 * S.max_reg;
     uint64_t *regV = S.reg_v + (size_t)slot * 2 * S.max_reg;
     uint32_t stamp = EXACT ? 0u : S.stamp[slot];   // the same in every thread, advanced together
-    heavy_zero<EXACT>(sm, S, V);
+    heavy_zero<EXACT, GBM>(sm, S, V);
     hsync<WARP>();
 
     // written before this launch by earlier work on the stream: the same in every thread
@@ -1372,7 +1416,7 @@ heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy
         if (tid == 0) V.load = 0;
         hsync<WARP>();
         HeavyRun r{t_start, nreg0, 0, 0, -1, -1, 0};
-        if (WARP) heavy_run_fault_warp<EXACT>(D, f, fid, tend, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
+        if (WARP) heavy_run_fault_warp<EXACT, GBM>(D, f, fid, tend, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
         else heavy_run_fault<EXACT>(D, f, fid, tend, q.fault_budget, sm, V, fval, stamp, regR, regV, S.max_reg, S.max_net, r);
         hsync<WARP>();
         const bool carry = r.status == 0 && tend < D.T;   // alive at the end of the window
@@ -2086,15 +2130,17 @@ cudaError_t launch_light_window(const DevDesign *d_designs, DevFaults f, WinLigh
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
-size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net, bool exact) {
+size_t heavy_smem_bytes(uint32_t max_node, uint32_t max_levels, uint32_t max_net, bool exact, bool gbm) {
     const size_t side = exact ? (size_t)(max_net + 31) / 32 + HEAVY_DLIST : HEAVY_FILTER / 32;
-    size_t words = (size_t)(max_node + 31) / 32 + max_levels + HEAVY_NLIST + side;
+    size_t words = heavy_node_words(max_node, gbm) + max_levels + HEAVY_NLIST + side;
     words = (words + 1) & ~(size_t)1;   // 8-byte alignment of the range list
     return words * sizeof(uint32_t) + HEAVY_FRANGE * sizeof(uint2) +
            (size_t)((max_levels + 63) / 64) * sizeof(unsigned long long);
 }
 
-static const void *heavy_fn(bool window, int block, bool exact) {
+static const void *heavy_fn(bool window, int block, bool exact, bool gbm = false) {
+    if (gbm)   // one warp per fault, stamped net record
+        return window ? (const void *)heavy_window_kernel<true, false, true> : (const void *)heavy_kernel<true, false, true>;
     if (window)
         return block == 32 ? (exact ? (const void *)heavy_window_kernel<true, true> : (const void *)heavy_window_kernel<true, false>)
                            : (exact ? (const void *)heavy_window_kernel<false, true> : (const void *)heavy_window_kernel<false, false>);
@@ -2102,9 +2148,9 @@ static const void *heavy_fn(bool window, int block, bool exact) {
                        : (exact ? (const void *)heavy_kernel<false, true> : (const void *)heavy_kernel<false, false>);
 }
 
-int heavy_max_blocks_per_sm(int block, size_t smem, bool exact) {
+int heavy_max_blocks_per_sm(int block, size_t smem, bool exact, bool gbm) {
     int n = 0;
-    const void *fn = heavy_fn(true, block, exact);
+    const void *fn = heavy_fn(true, block, exact, gbm);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem);
     return n;
@@ -2112,8 +2158,8 @@ int heavy_max_blocks_per_sm(int block, size_t smem, bool exact) {
 
 cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, HeavyScratch s,
                          int block, int grid, cudaStream_t stream) {
-    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net, s.exact != 0);
-    const void *fn = heavy_fn(false, block, s.exact != 0);
+    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net, s.exact != 0, s.gbm != nullptr);
+    const void *fn = heavy_fn(false, block, s.exact != 0, s.gbm != nullptr);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_designs, (void *)&f, (void *)&q, (void *)&s};
@@ -2122,8 +2168,8 @@ cudaError_t launch_heavy(const DevDesign *d_designs, DevFaults f, Queues q, Heav
 
 cudaError_t launch_heavy_window(const DevDesign *d_designs, DevFaults f, WinHeavy w, HeavyScratch s,
                                 int block, int grid, cudaStream_t stream) {
-    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net, s.exact != 0);
-    const void *fn = heavy_fn(true, block, s.exact != 0);
+    const size_t smem = heavy_smem_bytes(s.max_node, s.max_levels, s.max_net, s.exact != 0, s.gbm != nullptr);
+    const void *fn = heavy_fn(true, block, s.exact != 0, s.gbm != nullptr);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_designs, (void *)&f, (void *)&w, (void *)&s};

@@ -79,7 +79,7 @@ def _check_stopped(res, final, stop, no_drop):
 
 OPTS = [dict(window=64, heavy_frac=0.3), dict(window=64, heavy_frac=0.0, light_cap=1),
         dict(window=64, heavy_frac=1.0, heavy_form=2), dict(window=128, heavy_frac=0.3, no_drop=1),
-        dict(window=64, heavy_frac=0.3, no_drop=1, heavy_form=1)]
+        dict(window=64, heavy_frac=0.3, no_drop=1, heavy_form=1), dict(window=64, heavy_frac=1.0, heavy_form=3)]
 
 
 @pytest.mark.parametrize("opts", OPTS)

@@ -18,7 +18,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cou
 
 FORMS = [dict(), dict(window=32), dict(heavy_frac=1.0), dict(window=64, heavy_frac=0.3),
          dict(window=64, heavy_frac=1.0), dict(use_graph=1), dict(light_cap=1), dict(good_cluster=4),
-         dict(window=64, heavy_frac=1.0, heavy_form=2), dict(heavy_frac=1.0, heavy_form=2)]
+         dict(window=64, heavy_frac=1.0, heavy_form=2), dict(heavy_frac=1.0, heavy_form=2),
+         dict(window=64, heavy_frac=1.0, heavy_form=3), dict(heavy_frac=1.0, heavy_form=3)]
 
 
 @pytest.fixture(scope="module", autouse=True)

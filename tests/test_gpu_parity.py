@@ -83,6 +83,8 @@ OPTION_SETS = [
     dict(),
     dict(heavy_frac=1.0, heavy_form=2),
     dict(heavy_frac=0.3, heavy_form=2, heavy_block=128),
+    dict(heavy_frac=1.0, heavy_form=3),
+    dict(heavy_frac=0.2, heavy_form=3, heavy_ctas=5),
     dict(scheduler=rtlfs.SCHED_PLAIN),
     dict(heavy_frac=0.05),
     dict(heavy_frac=1.0),
@@ -224,7 +226,9 @@ def test_heavy_forms_alternate_on_one_context():
         sim.add(d, stim, u)
         ref = None
         for kw in (dict(heavy_form=1), dict(heavy_form=2), dict(heavy_form=1, window=64),
-                   dict(heavy_form=2, window=64), dict(heavy_form=2), dict(heavy_form=1)):
+                   dict(heavy_form=2, window=64), dict(heavy_form=2), dict(heavy_form=1),
+                   dict(heavy_form=3), dict(heavy_form=3, window=64), dict(heavy_form=1, window=64),
+                   dict(heavy_form=3), dict(heavy_form=2)):
             res, loads = sim.run(want_load=True, heavy_frac=1.0, **kw)
             assert_same(split(res[0]), exp, str(kw))
             if ref is None:
@@ -241,7 +245,8 @@ def test_loads_are_schedule_independent():
     a = gpu_run(d, stim, u, want_load=True, heavy_frac=0.0)[3]
     b = gpu_run(d, stim, u, want_load=True, heavy_frac=1.0)[3]
     c = gpu_run(d, stim, u, want_load=True, heavy_frac=1.0, heavy_form=2)[3]
-    assert np.array_equal(a, b) and np.array_equal(a, c)
+    e = gpu_run(d, stim, u, want_load=True, heavy_frac=1.0, heavy_form=3)[3]
+    assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, e)
     assert a.sum() > 0
 
 
@@ -293,9 +298,10 @@ def test_error_codes():
         # the context stays usable after the rejected calls
         rtlfs.rtlfs_set_stimulus(ctx, did, synth.stimulus(good, 30, 1))
         rtlfs.rtlfs_set_faults(ctx, did, rtlfs.fault_array(synth.sample_faults(good, 50, 1)))
-        with pytest.raises(rtlfs.RtlfsError) as e:
-            rtlfs.rtlfs_run(ctx, [50], rtlfs.make_opts(good_staging=2))
-        assert e.value.code == rtlfs.RTLFS_E_ARG
+        for bad_opts in (dict(good_staging=2), dict(heavy_form=4), dict(heavy_form=3, heavy_block=64)):
+            with pytest.raises(rtlfs.RtlfsError) as e:
+                rtlfs.rtlfs_run(ctx, [50], rtlfs.make_opts(**bad_opts))
+            assert e.value.code == rtlfs.RTLFS_E_ARG
         res, _, _ = rtlfs.rtlfs_run(ctx, [50])
         assert len(res[0]) == 50
     finally:
@@ -355,7 +361,8 @@ def test_windowed_matches_oracle(window):
     u = synth.sample_faults(d, 3000, 27)
     exp = oracle.fault_sim(d, stim, u, threads=16)
     for kw in (dict(), dict(heavy_frac=0.1), dict(scheduler=rtlfs.SCHED_PLAIN, light_cap=1),
-               dict(heavy_frac=1.0), dict(heavy_frac=1.0, heavy_form=2), dict(heavy_form=2, heavy_block=64)):
+               dict(heavy_frac=1.0), dict(heavy_frac=1.0, heavy_form=2), dict(heavy_form=2, heavy_block=64),
+               dict(heavy_frac=1.0, heavy_form=3), dict(heavy_frac=0.1, heavy_form=3)):
         got = gpu_run(d, stim, u, want_load=True, window=window, **kw)
         assert_same(got, exp, f"window {window} {kw}")
     ref = gpu_run(d, stim, u, want_load=True)
