@@ -184,6 +184,7 @@ struct rtlfs_ctx {
         bool valid = false;
         uint32_t window = 0;              // first window still to run
         uint32_t W = 0, F = 0, nodrop = 0;
+        uint32_t lcap = 0;                // light capacity variant (its register-diff bound)
         std::vector<uint32_t> T, n_net;   // per design
         std::vector<uint8_t> det, st_nreg;
         std::vector<int32_t> cycle, port;
@@ -929,8 +930,9 @@ int set_faults_impl(rtlfs_ctx *ctx, uint32_t design_id, uint32_t n_faults, bool 
 namespace {
 
 // Whether the context can continue the checkpoint: same fault count, designs, stimulus
-// lengths, net counts, window and no-drop mode.
-int checkpoint_matches(rtlfs_ctx *ctx, const rtlfs_ctx::Checkpoint &c, uint32_t W, bool nodrop) {
+// lengths, net counts, window, no-drop mode and light capacity (the light lanes' register
+// diffs were bounded by it).
+int checkpoint_matches(rtlfs_ctx *ctx, const rtlfs_ctx::Checkpoint &c, uint32_t W, bool nodrop, int lcap) {
     if (!c.valid) return fail(ctx, RTLFS_E_STATE, "no checkpoint to resume from");
     if (c.F != ctx->F || c.T.size() != ctx->designs.size())
         return fail(ctx, RTLFS_E_ARG, "checkpoint was taken on other fault lists or designs");
@@ -939,17 +941,19 @@ int checkpoint_matches(rtlfs_ctx *ctx, const rtlfs_ctx::Checkpoint &c, uint32_t 
             return fail(ctx, RTLFS_E_ARG, "checkpoint design %zu differs from the context's", d);
     if (c.W != W) return fail(ctx, RTLFS_E_ARG, "resume needs the checkpoint's window (%u)", c.W);
     if (c.nodrop != (nodrop ? 1u : 0u)) return fail(ctx, RTLFS_E_ARG, "resume needs the checkpoint's no_drop mode");
+    if (lcap >= 0 && c.lcap != (uint32_t)lcap)
+        return fail(ctx, RTLFS_E_ARG, "resume needs the checkpoint's light_cap (%u)", c.lcap + 1);
     return RTLFS_OK;
 }
 
 // Copy the campaign state after window w_end - 1 to the host (after the stream has drained).
 // pending[f] marks the faults still alive at the stop.
-int take_checkpoint(rtlfs_ctx *ctx, uint32_t nw, uint32_t w_end, uint32_t W, bool nodrop,
+int take_checkpoint(rtlfs_ctx *ctx, uint32_t nw, uint32_t w_end, uint32_t W, bool nodrop, int lcap,
                     std::vector<uint8_t> *pending) {
     rtlfs_ctx::Checkpoint &c = ctx->ck;
     const uint32_t F = ctx->F, wl = w_end - 1;
     c = rtlfs_ctx::Checkpoint{};
-    c.window = w_end; c.W = W; c.F = F; c.nodrop = nodrop ? 1u : 0u;
+    c.window = w_end; c.W = W; c.F = F; c.nodrop = nodrop ? 1u : 0u; c.lcap = (uint32_t)lcap;
     for (Design *D : ctx->designs) { c.T.push_back(D->T); c.n_net.push_back(D->n_net); }
     uint32_t n_live = 0, n_carry = 0;
     unsigned long long pool_top = 0;
@@ -1034,7 +1038,7 @@ int restore_checkpoint(rtlfs_ctx *ctx, uint32_t nw, uint32_t w_begin, uint32_t *
 constexpr char CK_MAGIC[8] = {'R', 'T', 'L', 'F', 'S', 'C', 'K', '1'};
 struct CkHeader {
     char magic[8];
-    uint32_t n_designs, F, W, window, nodrop, n_live, n_carry, reserved;
+    uint32_t n_designs, F, W, window, nodrop, n_live, n_carry, lcap;
     uint64_t pool_top, n_rows;
 };
 
@@ -1326,7 +1330,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     const uint32_t w_end = stopping ? (uint32_t)o.stop_cycle / W : nw;
     uint32_t w_begin = 0;
     if (resuming) {
-        int rc2 = checkpoint_matches(ctx, ctx->ck, W, nodrop);
+        int rc2 = checkpoint_matches(ctx, ctx->ck, W, nodrop, lcap);
         if (rc2 != RTLFS_OK) return rc2;
         w_begin = ctx->ck.window;
         if (w_begin >= w_end) return fail(ctx, RTLFS_E_ARG, "stop_cycle is not after the checkpoint");
@@ -1593,7 +1597,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     ctx->mism_valid = nodrop && !stopping;
     std::vector<uint8_t> pending;
     if (stopping) {
-        rc = take_checkpoint(ctx, nw, w_end, W, nodrop, &pending);
+        rc = take_checkpoint(ctx, nw, w_end, W, nodrop, lcap, &pending);
         if (rc != RTLFS_OK) return rc;
     } else {
         ctx->ck.valid = false;   // the campaign ran to its end
@@ -1981,6 +1985,7 @@ int rtlfs_checkpoint_save(rtlfs_ctx *ctx, void *buf, uint64_t bytes) {
     CkHeader h{};
     memcpy(h.magic, CK_MAGIC, 8);
     h.n_designs = (uint32_t)c.T.size(); h.F = c.F; h.W = c.W; h.window = c.window; h.nodrop = c.nodrop;
+    h.lcap = c.lcap;
     h.n_live = (uint32_t)c.live.size(); h.n_carry = (uint32_t)c.carry.size();
     h.pool_top = c.pool_r.size(); h.n_rows = c.rows.size();
     unsigned char *p = static_cast<unsigned char *>(buf);
@@ -2003,7 +2008,7 @@ int rtlfs_checkpoint_load(rtlfs_ctx *ctx, const void *buf, uint64_t bytes) {
     memcpy(&h, buf, sizeof(h));
     if (memcmp(h.magic, CK_MAGIC, 8) != 0) return fail(ctx, RTLFS_E_ARG, "not a checkpoint");
     const uint64_t F = h.F, nd = h.n_designs;
-    if (h.W == 0 || h.window == 0 || h.n_live > F || h.n_carry > F || h.nodrop > 1 || nd > 65535)
+    if (h.W == 0 || h.window == 0 || h.n_live > F || h.n_carry > F || h.nodrop > 1 || nd > 65535 || h.lcap > 2)
         return fail(ctx, RTLFS_E_ARG, "malformed checkpoint header");
     // sizes the header implies, then the byte count must agree exactly
     rtlfs_ctx::Checkpoint c;
@@ -2022,11 +2027,27 @@ int rtlfs_checkpoint_load(rtlfs_ctx *ctx, const void *buf, uint64_t bytes) {
     uint64_t rows = 0;
     for (uint32_t n : c.n_net) rows += n;
     if (rows != h.n_rows) return fail(ctx, RTLFS_E_ARG, "checkpoint rows do not match its designs");
-    for (uint32_t f : c.live) if (f >= F) return fail(ctx, RTLFS_E_ARG, "checkpoint names a fault out of range");
-    for (const HeavyCarry &x : c.carry)
-        if (x.fault >= F || x.off + x.nreg > h.pool_top) return fail(ctx, RTLFS_E_ARG, "checkpoint carry out of range");
-    c.window = h.window; c.W = h.W; c.F = h.F; c.nodrop = h.nodrop; c.valid = true;
-    rc = checkpoint_matches(ctx, c, c.W, c.nodrop != 0);
+    // everything the kernels index with: fault ids, register-diff counts within the bounds
+    // the kernels were built for, register ids within the fault's design
+    if (F != ctx->F || nd != ctx->designs.size())
+        return fail(ctx, RTLFS_E_ARG, "checkpoint was taken on other fault lists or designs");
+    std::vector<uint32_t> regs_of(F, 0);
+    for (size_t d = 0; d < ctx->designs.size(); ++d)
+        for (uint32_t f = ctx->f_first[d]; f < ctx->f_first[d + 1]; ++f) regs_of[f] = ctx->designs[d]->R;
+    const uint32_t kr = (uint32_t)LIGHT_CAPS[h.lcap][0];
+    for (uint32_t f : c.live) {
+        if (f >= F || c.st_nreg[f] > kr) return fail(ctx, RTLFS_E_ARG, "checkpoint light fault out of range");
+        for (uint32_t k = 0; k < c.st_nreg[f]; ++k)
+            if (c.st_r[(size_t)k * F + f] >= regs_of[f]) return fail(ctx, RTLFS_E_ARG, "checkpoint register out of range");
+    }
+    for (const HeavyCarry &x : c.carry) {
+        if (x.fault >= F || x.nreg > regs_of[x.fault] || x.off + x.nreg > h.pool_top)
+            return fail(ctx, RTLFS_E_ARG, "checkpoint carry out of range");
+        for (uint32_t k = 0; k < x.nreg; ++k)
+            if (c.pool_r[x.off + k] >= regs_of[x.fault]) return fail(ctx, RTLFS_E_ARG, "checkpoint register out of range");
+    }
+    c.window = h.window; c.W = h.W; c.F = h.F; c.nodrop = h.nodrop; c.lcap = h.lcap; c.valid = true;
+    rc = checkpoint_matches(ctx, c, c.W, c.nodrop != 0, -1);
     if (rc != RTLFS_OK) return rc;
     ctx->ck = std::move(c);
     ctx->err.clear();

@@ -196,3 +196,53 @@ def test_checkpoint_errors():
     full_res, _, _, _ = _full(2, **opts)
     for a, b in zip(res, full_res):
         assert np.array_equal(a, b)
+
+
+def _layout(blob):
+    """Offsets of the checkpoint fields (the saved layout: a 56-byte header, then the per-design
+    and per-fault arrays in a fixed order)."""
+    h = np.frombuffer(blob[:56], np.uint8)
+    u32 = h[8:40].view(np.uint32)
+    nd, F, n_live, n_carry = int(u32[0]), int(u32[1]), int(u32[5]), int(u32[6])
+    pool_top = int(h[40:48].view(np.uint64)[0])
+    off, o = {}, 56
+    for name, size in (("T", 4 * nd), ("n_net", 4 * nd), ("det", F), ("cycle", 4 * F), ("port", 4 * F),
+                       ("load", 8 * F), ("mism", 4 * F), ("st_nreg", F), ("st_r", 32 * F), ("st_v", 64 * F),
+                       ("live", 4 * n_live), ("carry", 16 * n_carry), ("pool_r", 4 * pool_top)):
+        off[name] = o
+        o += size
+    return off, F, n_live, n_carry, pool_top
+
+
+def test_checkpoint_contents_checked():
+    """A loaded checkpoint is checked against the kernels' bounds: a live light fault with
+    more register diffs than its light capacity holds, a carried heavy fault naming a
+    register outside its design, and a resume under another light capacity are refused."""
+    opts = dict(window=64, heavy_frac=0.3, light_cap=1)
+    with _sim() as sim:
+        sim.run(stop_cycle=64, **opts)
+        blob = sim.checkpoint()
+        with pytest.raises(RtlfsError):          # other light capacity
+            sim.run(resume=1, **{**opts, "light_cap": 2})
+    off, F, n_live, n_carry, pool_top = _layout(blob)
+    assert n_live > 0
+    live0 = int(np.frombuffer(blob, np.uint32, 1, off["live"])[0])
+    bad = bytearray(blob)
+    bad[off["st_nreg"] + live0] = 5               # light capacity 1 holds 4
+    with _sim() as sim:
+        with pytest.raises(RtlfsError):
+            sim.restore(bytes(bad))
+    carry0 = np.frombuffer(blob, np.uint32, 4, off["carry"]) if n_carry else np.zeros(4, np.uint32)
+    if int(carry0[1]) > 0:                        # nreg of the first carry
+        bad = bytearray(blob)
+        pos = off["pool_r"] + 4 * int(np.frombuffer(blob, np.uint64, 1, off["carry"] + 8)[0])
+        bad[pos:pos + 4] = np.uint32(0xFFFFFF).tobytes()
+        with _sim() as sim:
+            with pytest.raises(RtlfsError):
+                sim.restore(bytes(bad))
+    with _sim() as sim:                           # the untouched blob resumes
+        sim.restore(blob)
+        res, _ = sim.run(resume=1, **opts)
+    full_res, _, _, _ = _full(2, **opts)
+    for a, b in zip(res, full_res):
+        assert np.array_equal(a, b)
