@@ -158,7 +158,8 @@ typedef struct {
                                 detected = RTLFS_PENDING */
     int32_t  resume;         /* 1: continue the campaign from the checkpoint held by the context
                                 (made by a stopped run or rtlfs_checkpoint_load); the other
-                                options must match the stopped run's window and no_drop */
+                                options must match the stopped run's window, no_drop and
+                                light_cap (RTLFS_E_ARG otherwise) */
     int32_t  heavy_form;     /* heavy kernel's record of differing nets: 0 = auto (the
                                 exact one unless it costs resident CTAs), 1 = a shared-memory
                                 bit per net, 2 = a small shared filter plus cycle stamps on
@@ -274,7 +275,8 @@ int rtlfs_get_stats(const rtlfs_ctx *ctx, rtlfs_stats *out);
  *   rtlfs_checkpoint_size: bytes the current checkpoint takes (RTLFS_E_STATE: none held).
  *   rtlfs_checkpoint_save: write it into buf[bytes] (RTLFS_E_ARG if bytes is too small).
  *   rtlfs_checkpoint_load: take a checkpoint into a context holding the same designs,
- *     stimuli and fault lists (RTLFS_E_ARG on a malformed buffer or a mismatch); the next
+ *     stimuli and fault lists (RTLFS_E_ARG on a malformed buffer or a mismatch, including
+ *     register-diff counts or register ids outside the bounds the kernels use); the next
  *     rtlfs_run with resume = 1 continues from it. */
 #define RTLFS_PENDING 254   /* rtlfs_result.detected of a fault still alive at stop_cycle */
 int rtlfs_checkpoint_size(rtlfs_ctx *ctx, uint64_t *bytes);
