@@ -1,5 +1,7 @@
-"""Autotuner for the campaign knobs: light-lane capacity, light/heavy CTA sizes and the
-fraction of faults the scheduler sends to the heavy kernel from cycle 0.
+"""Autotuner for the campaign knobs: cycle windows (overlapped good-trace, light and heavy
+kernels) or one pass, light-lane capacity, and the fraction of faults the scheduler sends to
+the heavy kernel from cycle 0 (one warp per heavy fault, the heavy form the host picks by
+occupancy).
 
 Every candidate is timed with real campaigns through rtlfs_run on the workload loaded in
 the simulator (device-event time of the whole campaign, best of `repeats`); the fastest
@@ -22,10 +24,10 @@ CACHE = os.path.join(HERE, "autotune_cache.json")
 def candidates(with_mlp: bool) -> List[Dict]:
     out = []
     sched = SCHED_MLP if with_mlp else SCHED_HEURISTIC
-    for cap in (1, 2):
-        for hb in (32, 64):
-            for hf in (0.0, 0.03, 0.08):
-                out.append(dict(scheduler=sched, light_cap=cap, heavy_block=hb, heavy_frac=hf))
+    for window in (256, 0):
+        for cap in (1, 2):
+            for hf in (0.0, 0.05):
+                out.append(dict(scheduler=sched, window=window, light_cap=cap, heavy_frac=hf))
     return out
 
 
