@@ -124,40 +124,77 @@ int oracle_topo_order(const oracle_design *d, int32_t *order)
     return rc;
 }
 
-/* Evaluate node i from the current net values. */
-static uint64_t eval_node(const oracle_design *d, const uint64_t *net, int32_t i)
+/* One node in evaluation (topological) order with its operands resolved once per call:
+ * the op code, the net it drives, its operand nets (0 where the op reads fewer), its
+ * constant, the mask of its width and, for CONCAT, the width of operand b. An op code
+ * outside the op set gives 0. */
+typedef struct {
+    uint32_t op, out, a, b, c, wb;
+    uint64_t imm, mask;
+} oracle_step;
+
+enum { O_NONE = 14 };
+
+static int nops_of(unsigned op)
 {
-    uint64_t a = net[d->a[i]], b = 0, c = 0, r = 0, k = d->imm[i];
-    switch (d->op[i]) {
-    case O_AND:    b = net[d->b[i]]; r = a & b; break;
-    case O_OR:     b = net[d->b[i]]; r = a | b; break;
-    case O_XOR:    b = net[d->b[i]]; r = a ^ b; break;
-    case O_NOT:    r = ~a; break;
-    case O_ADD:    b = net[d->b[i]]; r = a + b; break;
-    case O_SUB:    b = net[d->b[i]]; r = a - b; break;
-    case O_MUX2:   b = net[d->b[i]]; c = net[d->c[i]]; r = (a != 0) ? b : c; break;
-    case O_EQ:     b = net[d->b[i]]; r = (a == b) ? 1 : 0; break;
-    case O_LT:     b = net[d->b[i]]; r = (a < b) ? 1 : 0; break;
-    case O_SHL:    r = k >= 64 ? 0 : (a << k); break;
-    case O_SHR:    r = k >= 64 ? 0 : (a >> k); break;
-    case O_SLICE:  r = k >= 64 ? 0 : (a >> k); break;
-    case O_CONCAT: {
-        unsigned wb = net_width(d, d->b[i]);
-        b = net[d->b[i]];
-        r = (wb >= 64 ? 0 : (a << wb)) | b;
-        break;
+    return op == O_CONST ? 0 : (op == O_NOT || op == O_SHL || op == O_SHR || op == O_SLICE) ? 1
+         : op == O_MUX2 ? 3 : op < O_NONE ? 2 : 0;
+}
+
+/* The nodes in a topological order as a list of steps. Returns a malloc'd array, or
+ * NULL on a combinational cycle. */
+static oracle_step *oracle_program(const oracle_design *d)
+{
+    int32_t N = d->n_node, base = d->n_in + d->n_reg;
+    int32_t *order = malloc(sizeof(int32_t) * ((size_t)N + 1));
+    if (oracle_topo_order(d, order) != 0) { free(order); return NULL; }
+    oracle_step *prog = malloc(sizeof(oracle_step) * ((size_t)N + 1));
+    for (int32_t k = 0; k < N; k++) {
+        int32_t i = order[k];
+        oracle_step *s = &prog[k];
+        int nops = nops_of(d->op[i]);
+        s->op = d->op[i] < O_NONE ? d->op[i] : O_NONE;
+        s->out = (uint32_t)(base + i);
+        s->a = nops >= 1 ? d->a[i] : 0;
+        s->b = nops >= 2 ? d->b[i] : 0;
+        s->c = nops >= 3 ? d->c[i] : 0;
+        s->wb = s->op == O_CONCAT ? net_width(d, d->b[i]) : 0;
+        s->imm = d->imm[i];
+        s->mask = mask_of(d->w[i]);
     }
-    case O_CONST:  r = k; break;
-    default:       r = 0; break;
-    }
-    return r & mask_of(d->w[i]);
+    free(order);
+    return prog;
+}
+
+/* Evaluate one node from the current net values. Every op's value is computed and the
+ * node's op code picks its own: a table instead of a branch per op, because the ops of
+ * consecutive nodes are unrelated and a branch on them is mispredicted on most nodes. */
+static uint64_t eval_step(const oracle_step *s, const uint64_t *net)
+{
+    uint64_t a = net[s->a], b = net[s->b], c = net[s->c], k = s->imm, r[O_NONE + 1];
+    r[O_AND]    = a & b;
+    r[O_OR]     = a | b;
+    r[O_XOR]    = a ^ b;
+    r[O_NOT]    = ~a;
+    r[O_ADD]    = a + b;
+    r[O_SUB]    = a - b;
+    r[O_MUX2]   = (a != 0) ? b : c;
+    r[O_EQ]     = (a == b) ? 1 : 0;
+    r[O_LT]     = (a < b) ? 1 : 0;
+    r[O_SHL]    = k >= 64 ? 0 : (a << k);
+    r[O_SHR]    = k >= 64 ? 0 : (a >> k);
+    r[O_SLICE]  = k >= 64 ? 0 : (a >> k);
+    r[O_CONCAT] = (s->wb >= 64 ? 0 : (a << s->wb)) | b;
+    r[O_CONST]  = k;
+    r[O_NONE]   = 0;
+    return r[s->op] & s->mask;
 }
 
 /* One machine over T cycles. With fault_net < 0 this is the good machine: it fills
  * gout[T][n_out]. Otherwise it compares against gout and returns the first detection
  * through *cycle and *port (both -1 if never detected) and the number of cycles with a
  * differing port through *mism. */
-static void run_machine(const oracle_design *d, const int32_t *order, int32_t T,
+static void run_machine(const oracle_design *d, const oracle_step *prog, int32_t T,
                         const uint64_t *stim, uint64_t *gout_w, const uint64_t *gout_r,
                         uint64_t *trace_w,
                         int64_t fault_net, unsigned fault_bit, unsigned fault_val,
@@ -189,9 +226,9 @@ static void run_machine(const oracle_design *d, const int32_t *order, int32_t T,
             FORCE(I + r);
         }
         for (int32_t k = 0; k < N; k++) {
-            int32_t n = order[k];
-            net[I + R + n] = eval_node(d, net, n);
-            FORCE(I + R + n);
+            const oracle_step *st = &prog[k];
+            net[st->out] = eval_step(st, net);
+            FORCE(st->out);
         }
         if (trace_w) memcpy(trace_w + (size_t)t * (I + R + N), net, sizeof(uint64_t) * (I + R + N));
         if (fault_net < 0) {
@@ -225,14 +262,14 @@ static size_t n_nets(const oracle_design *d) { return (size_t)d->n_in + d->n_reg
 int oracle_good_run(const oracle_design *d, int32_t T, const uint64_t *stim, uint64_t *gout,
                     uint64_t *trace)
 {
-    int32_t *order = malloc(sizeof(int32_t) * ((size_t)d->n_node + 1));
-    if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
+    oracle_step *prog = oracle_program(d);
+    if (!prog) return -1;
     uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
     uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
     int32_t cy, po;
     uint32_t mi;
-    run_machine(d, order, T, stim, gout, NULL, trace, -1, 0, 0, -1, 0, net, Q, &cy, &po, &mi);
-    free(order); free(net); free(Q);
+    run_machine(d, prog, T, stim, gout, NULL, trace, -1, 0, 0, -1, 0, net, Q, &cy, &po, &mi);
+    free(prog); free(net); free(Q);
     return 0;
 }
 
@@ -243,17 +280,17 @@ int oracle_fault_sim(const oracle_design *d, int32_t T, const uint64_t *stim,
                      const uint8_t *fbit, const uint8_t *fval,
                      uint8_t *detected, int32_t *cycle, int32_t *port)
 {
-    int32_t *order = malloc(sizeof(int32_t) * ((size_t)d->n_node + 1));
-    if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
+    oracle_step *prog = oracle_program(d);
+    if (!prog) return -1;
     uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
     uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
     uint32_t mi;
     for (int32_t f = 0; f < F; f++) {
-        run_machine(d, order, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fval[f],
+        run_machine(d, prog, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fval[f],
                     -1, 0, net, Q, &cycle[f], &port[f], &mi);
         detected[f] = cycle[f] >= 0 ? 1 : 0;
     }
-    free(order); free(net); free(Q);
+    free(prog); free(net); free(Q);
     return 0;
 }
 
@@ -266,16 +303,16 @@ int oracle_fault_sim_ex(const oracle_design *d, int32_t T, const uint64_t *stim,
                         int32_t no_drop, uint8_t *detected, int32_t *cycle, int32_t *port,
                         uint32_t *mism)
 {
-    int32_t *order = malloc(sizeof(int32_t) * ((size_t)d->n_node + 1));
-    if (oracle_topo_order(d, order) != 0) { free(order); return -1; }
+    oracle_step *prog = oracle_program(d);
+    if (!prog) return -1;
     uint64_t *net = malloc(sizeof(uint64_t) * (n_nets(d) + 1));
     uint64_t *Q = malloc(sizeof(uint64_t) * ((size_t)d->n_reg + 1));
     for (int32_t f = 0; f < F; f++) {
         int64_t fc = fkind[f] >= 2 ? (int64_t)fcycle[f] : -1;
-        run_machine(d, order, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fkind[f],
+        run_machine(d, prog, T, stim, NULL, gout, NULL, (int64_t)fnet[f], fbit[f], fkind[f],
                     fc, no_drop, net, Q, &cycle[f], &port[f], &mism[f]);
         detected[f] = cycle[f] >= 0 ? 1 : 0;
     }
-    free(order); free(net); free(Q);
+    free(prog); free(net); free(Q);
     return 0;
 }

@@ -491,9 +491,22 @@ def sample_faults(design: Design, F: int, seed: int) -> Faults:
 
 # ---- named workloads -----------------------------------------------------------------
 
+def batch_workload(seed0: int = 1000, count: int = 64) -> List[Tuple[Design, np.ndarray, Faults]]:
+    """The batched campaign: the `count` designs of batch_designs(seed0, count), design i
+    with its own uniform random stimulus of T_i cycles (seed 1_000_000 + seed0 + i) and
+    F_i stuck-at faults sampled from its universe (seed 2_000_000 + seed0 + i).
+    Returns (design, stimulus, faults) triples."""
+    out = []
+    for i, (d, T, F) in enumerate(batch_designs(seed0, count)):
+        out.append((d, stimulus(d, T, 1_000_000 + seed0 + i),
+                    sample_faults(d, F, 2_000_000 + seed0 + i)))
+    return out
+
+
 def workload(name: str):
-    """(design, stimulus, faults) for a named workload shape. Sizes follow the five
-    campaign configurations: tiny (config 1), medium (config 2), large (config 4)."""
+    """(design, stimulus, faults) for a named single-design workload shape: tiny (200
+    nodes, full fault list), medium (20k nodes, 100k faults), large (200k nodes, 1M
+    faults). The 64-design batch is batch_workload()."""
     if name == "tiny":
         d = tiny_design(1)
         return d, stimulus(d, 100, 101), fault_universe(d)

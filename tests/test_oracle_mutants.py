@@ -21,16 +21,19 @@ from paper_2508_16376_gb300 import synth
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle_sim.c")
 
 MUTANTS = {
-    "sub_operands_swapped": ("r = a - b;", "r = b - a;"),
-    "lt_not_strict": ("r = (a < b) ? 1 : 0;", "r = (a <= b) ? 1 : 0;"),
-    "mux_arms_swapped": ("r = (a != 0) ? b : c;", "r = (a != 0) ? c : b;"),
-    "concat_halves_swapped": ("r = (wb >= 64 ? 0 : (a << wb)) | b;",
-                              "r = (wb >= 64 ? 0 : (b << wb)) | a;"),
-    "no_result_mask": ("return r & mask_of(d->w[i]);", "return r;"),
+    "sub_operands_swapped": ("r[O_SUB]    = a - b;", "r[O_SUB]    = b - a;"),
+    "lt_not_strict": ("r[O_LT]     = (a < b) ? 1 : 0;", "r[O_LT]     = (a <= b) ? 1 : 0;"),
+    "mux_arms_swapped": ("r[O_MUX2]   = (a != 0) ? b : c;", "r[O_MUX2]   = (a != 0) ? c : b;"),
+    "concat_halves_swapped": ("r[O_CONCAT] = (s->wb >= 64 ? 0 : (a << s->wb)) | b;",
+                              "r[O_CONCAT] = (s->wb >= 64 ? 0 : (b << s->wb)) | a;"),
+    "no_result_mask": ("return r[s->op] & s->mask;", "return r[s->op];"),
+    "shr_as_shl": ("r[O_SHR]    = k >= 64 ? 0 : (a >> k);", "r[O_SHR]    = k >= 64 ? 0 : (a << k);"),
+    "concat_width_of_a": ("s->wb = s->op == O_CONCAT ? net_width(d, d->b[i]) : 0;",
+                          "s->wb = s->op == O_CONCAT ? net_width(d, d->a[i]) : 0;"),
     "no_force_on_reg_read": ("            net[I + r] = Q[r];\n            FORCE(I + r);",
                              "            net[I + r] = Q[r];"),
-    "no_force_on_node": ("            net[I + R + n] = eval_node(d, net, n);\n            FORCE(I + R + n);",
-                         "            net[I + R + n] = eval_node(d, net, n);"),
+    "no_force_on_node": ("            net[st->out] = eval_step(st, net);\n            FORCE(st->out);",
+                         "            net[st->out] = eval_step(st, net);"),
     "latch_without_mask": ("Q[r] = net[d->reg_d[r]] & mask_of(d->reg_w[r]);",
                            "Q[r] = net[d->reg_d[r]];"),
     "stuck_value_inverted": ("if (fault_val) m1 = (uint64_t)1 << fault_bit;",
