@@ -179,6 +179,13 @@ typedef struct {
                                 warp stages them into a shared-memory ring with bulk
                                 asynchronous copies (TMA) for the consumer threads. Same
                                 results; RTLFS_E_CUDA if a staging wait runs out */
+    int32_t  good_reserve;   /* windowed form: SMs kept free for the good trace while it is
+                                still running ahead of the faulty kernels. Until the last
+                                window's good trace is done, light and heavy CTAs that start
+                                on an SM whose id is below good_reserve leave at once (their
+                                faults go to the other CTAs through the work queues), so
+                                the good trace of later windows never waits for a window's
+                                faulty kernels to drain. 0 = none. Same results */
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */
@@ -311,8 +318,10 @@ int rtlfs_design_info(const rtlfs_ctx *ctx, uint32_t design_id, uint32_t *n_nets
  * reconvergence-counting cone estimate, / 20, at most 1.5), topological level of the site
  * (0 for inputs/registers, else (level+1)/n_levels), register depth from the site to the
  * nearest output (min(depth,16)/16; 1 if no output is reachable), width of the site net
- * / 64, and the good-trace toggle rate of the site bit (changes between consecutive
- * cycles / (T-1)).
+ * / 64, and the good-trace toggle rate of the site bit over the first P = min(T, 256)
+ * cycles (changes between consecutive cycles / (P-1); 0 when P = 1). The prefix is the
+ * same in every form of the campaign, so a windowed campaign orders its first window with
+ * the features the predictor was trained on.
  *
  * Network: 5 -> 64 (ReLU) -> 64 (ReLU) -> 1, RTLFS_MLP_PARAMS parameters laid out as
  * W1[5][64], b1[64], W2[64][64], b2[64], w3[64], b3 (W[i][j] connects unit i of one layer
@@ -346,32 +355,38 @@ int rtlfs_mlp_train(rtlfs_ctx *ctx, const float *X, const float *t, uint32_t n, 
                     uint32_t batch, float lr, float *final_loss);
 
 /* ---- allocation-free fault simulation -------------------------------------------------
- * The paper has no counterpart to this call; it exists for callers that must not allocate
- * device memory where they run: work issued while a stream is captured into a CUDA graph
- * (cudaMalloc would break the capture), latency-critical paths that cannot take an
- * allocation or the synchronisation it may imply, and hosts whose device memory is owned
- * by another allocator. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The paper has no counterpart to this call. It is for callers that cannot obtain device
+ * memory from cudaMalloc at the point where they simulate: a host process whose device
+ * memory is owned by another allocator (a framework's caching pool that has reserved the
+ * GPU's memory, which this library cannot call into), and latency-critical paths where
+ * the cost of an allocation, and the device-wide synchronisation cudaMalloc and cudaFree
+ * can imply, are not acceptable. The call allocates nothing: no cudaMalloc, cudaFree or
+ * other allocating routine.
  *
- * It simulates faults[n_faults] (device memory, the caller's net numbering) of design
- * design_id against that design's good trace, one thread per fault (the plain GPU form),
- * and writes results[n_faults] (device memory) with the same contract as rtlfs_run. The
- * context must already hold the design's current good trace (from rtlfs_run or
- * rtlfs_good_outputs after the last rtlfs_set_stimulus): RTLFS_E_STATE otherwise.
+ * It simulates faults[n_faults] (device memory, rtlfs_fault records in the caller's net
+ * numbering) of design design_id against that design's good trace, one thread per fault
+ * (the plain GPU form), and writes results[n_faults] (device memory, rtlfs_result records)
+ * with the same contract as rtlfs_run. Supported: stuck-at faults on input, register and
+ * node nets. Output-port ids (n_net + o) are not supported by this call: such a fault gets
+ * detected = 254 and the call returns RTLFS_E_ARG (rtlfs_run simulates them). The context
+ * must already hold the design's current good trace (from rtlfs_run or rtlfs_good_outputs
+ * after the last rtlfs_set_stimulus): RTLFS_E_STATE otherwise.
  *
  * Scratch: a file-scope device array of RTLFS_STATIC_SCRATCH_BYTES (64 MiB) inside the
  * library, held by every GPU that loads the library until the process exits. A design
- * needs 12 B per net + 8 B per node + 24 B per register of scratch per simultaneously
- * simulated fault (faults run in waves that fit); a design whose single fault does not
- * fit is rejected with RTLFS_E_ARG. Every call shares the array and leaves its contents
- * behind; the call clears what must start at zero. Calls whose work overlaps on the GPU
- * (other threads, other streams) race on the array: serialise them.
+ * needs 4 B per net once plus 12 B per net + 8 B per node + 24 B per register for every
+ * simultaneously simulated fault (faults run in waves that fit); a design whose single
+ * fault does not fit is rejected with RTLFS_E_ARG. Every call shares the array and leaves
+ * its contents behind; the call clears what must start at zero. Calls whose work overlaps
+ * on the GPU (other threads, other streams) race on the array: serialise them.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and keeps it; make that first call before any stream capture. The call enqueues on
- * `stream` (a cudaStream_t; null = the legacy default stream), waits for the stream, and
- * returns RTLFS_E_ARG if a fault's net, bit or stuck value is out of range (that fault's
- * result carries detected = 254). */
-#define RTLFS_STATIC_SCRATCH_BYTES (64u << 20)
+ * What a call does: it copies the design's net-number map (4 B per net) from host memory
+ * into the array, clears the wave's scratch, launches the kernel once per wave on `stream`
+ * (a cudaStream_t; null = the legacy default stream), copies a 4-byte error word back to
+ * the host and waits for `stream` before it returns. The first call on a device also looks
+ * up the array's device address (cudaGetSymbolAddress) and keeps it; make that first call
+ * before any stream capture. Returns RTLFS_E_ARG if a fault's net, bit or stuck value is
+ * out of range (that fault's result carries detected = 254). */
 int rtlfs_fault_sim_static(rtlfs_ctx *ctx, uint32_t design_id, const rtlfs_fault *faults,
                            uint32_t n_faults, rtlfs_result *results, void *stream);
 

@@ -8,7 +8,9 @@ W2[64][64], b2[64], w3[64], b3.
 
 The features are the plain definitions of the five per-fault inputs, computed from the
 design arrays and the oracle's good trace: static fan-out cone estimate, topological
-level, register depth to the outputs, width, and toggle rate of the site bit.
+level, register depth to the outputs, width, and toggle rate of the site bit over the
+first min(T, TOGGLE_CYCLES) cycles (the prefix a campaign has simulated when it orders its
+first cycle window).
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ from collections import deque
 import numpy as np
 
 IN, H = 5, 64
+TOGGLE_CYCLES = 256
 OFF_B1 = IN * H
 OFF_W2 = OFF_B1 + H
 OFF_B2 = OFF_W2 + H * H
@@ -152,7 +155,7 @@ def features(design, trace: np.ndarray, faults) -> np.ndarray:
                 depth[x] = d + 1
                 dq.append(x)
     widths = design.net_widths().astype(np.float64)
-    T = trace.shape[0]
+    T = min(trace.shape[0], TOGGLE_CYCLES)
     F = len(faults)
     X = np.zeros((F, 5), np.float64)
     for f in range(F):
@@ -161,6 +164,6 @@ def features(design, trace: np.ndarray, faults) -> np.ndarray:
         X[f, 1] = 0.0 if s < base else (level[s - base] + 1) / max(n_levels, 1)
         X[f, 2] = min(depth[s], 16) / 16.0
         X[f, 3] = widths[s] / 64.0
-        bits = (trace[:, s] >> np.uint64(b)) & np.uint64(1)
+        bits = (trace[:T, s] >> np.uint64(b)) & np.uint64(1)
         X[f, 4] = (np.count_nonzero(bits[1:] != bits[:-1]) / (T - 1)) if T > 1 else 0.0
     return X

@@ -1,34 +1,46 @@
-"""Autotuner for the campaign knobs: cycle windows (overlapped good-trace, light and heavy
-kernels) or one pass, light-lane capacity, and the fraction of faults the scheduler sends to
-the heavy kernel from cycle 0 (one warp per heavy fault, the heavy form the host picks by
-occupancy).
+"""Autotuner for the campaign knobs: the cycle-window length (overlapped good-trace, light
+and heavy kernels; 0 = one pass over all cycles), the light-lane capacity, the fraction of
+faults the scheduler sends to the heavy kernel from cycle 0 (the light/heavy split), and
+the CTA sizes of the light kernel (lanes per CTA) and of the heavy kernel (threads per
+heavy fault), and the SMs kept free for the good trace while it runs ahead (good_reserve).
 
 Every candidate is timed with real campaigns through rtlfs_run on the workload loaded in
-the simulator (device-event time of the whole campaign, best of `repeats`); the fastest
-candidate wins. Results never depend on the knobs, so tuning changes only time. Winners
-are cached per size bucket (log2 of total nets, cycles and faults) in a JSON file.
+the simulator (device-event time of the whole campaign, best of `repeats`). The search is
+coordinate descent: starting from BASE, each knob in turn takes the value that times
+fastest with the others held at the best so far, for `passes` passes. Results never depend
+on the knobs, so tuning changes only time. Winners are cached per size bucket (log2 of
+total nets, cycles and faults, and the design count) in a JSON file next to this module.
 """
 from __future__ import annotations
 
 import json
 import math
 import os
-from typing import Dict, List, Optional
+from typing import Dict, List, Optional, Sequence, Tuple
 
 from .rtlfs import SCHED_HEURISTIC, SCHED_MLP
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 
+BASE = dict(window=256, light_cap=1, heavy_frac=0.0, light_block=128, heavy_block=32, good_reserve=0)
+KNOBS: List[Tuple[str, Sequence]] = [
+    ("window", (256, 128, 512, 64, 0)),
+    ("light_cap", (1, 2)),
+    ("heavy_frac", (0.0, 0.02, 0.05)),
+    ("light_block", (128, 64, 256)),
+    ("heavy_block", (32, 64)),
+    ("good_reserve", (0, 32, 64)),
+]
 
-def candidates(with_mlp: bool) -> List[Dict]:
-    out = []
-    sched = SCHED_MLP if with_mlp else SCHED_HEURISTIC
-    for window in (256, 0):
-        for cap in (1, 2):
-            for hf in (0.0, 0.05):
-                out.append(dict(scheduler=sched, window=window, light_cap=cap, heavy_frac=hf))
-    return out
+
+def fixed_opts(sim, with_mlp: bool) -> Dict:
+    """Options every candidate shares: the scheduler, and graph replay for a batch of
+    designs (the whole campaign is one captured launch sequence)."""
+    o = dict(scheduler=SCHED_MLP if with_mlp else SCHED_HEURISTIC)
+    if len(sim.designs) > 1:
+        o["use_graph"] = 1
+    return o
 
 
 def size_bucket(sim) -> str:
@@ -39,6 +51,10 @@ def size_bucket(sim) -> str:
     return f"n{b(nets)}_t{b(cycles)}_f{b(faults)}_d{len(sim.designs)}"
 
 
+def cache_key(sim, with_mlp: bool) -> str:
+    return size_bucket(sim) + ("_mlp" if with_mlp else "")
+
+
 def _load_cache(path: str) -> dict:
     try:
         with open(path) as fh:
@@ -47,26 +63,48 @@ def _load_cache(path: str) -> dict:
         return {}
 
 
-def tune(sim, cands: Optional[List[Dict]] = None, repeats: int = 1, cache_path: str = CACHE,
-         use_cache: bool = True, with_mlp: bool = False, verbose: bool = False) -> Dict:
-    """Return the fastest option set for the campaign loaded in `sim` (a Simulator)."""
-    key = size_bucket(sim) + ("_mlp" if with_mlp else "")
+def cached(sim, with_mlp: bool = False, cache_path: str = CACHE) -> Optional[Dict]:
+    """The cached winner for the workload loaded in `sim`, or None."""
+    e = _load_cache(cache_path).get(cache_key(sim, with_mlp))
+    return dict(e["opts"]) if e else None
+
+
+def tune(sim, repeats: int = 1, passes: int = 1, cache_path: str = CACHE, use_cache: bool = True,
+         with_mlp: bool = False, knobs: Optional[List[Tuple[str, Sequence]]] = None,
+         verbose: bool = False) -> Dict:
+    """Return the fastest option set found for the campaign loaded in `sim` (a Simulator)."""
+    key = cache_key(sim, with_mlp)
     cache = _load_cache(cache_path) if use_cache else {}
     if use_cache and key in cache:
         return dict(cache[key]["opts"])
-    cands = cands or candidates(with_mlp)
-    best, best_ms, trials = None, float("inf"), []
-    for c in cands:
-        ms = float("inf")
-        for _ in range(repeats):
-            sim.run(**c)
-            ms = min(ms, sim.stats()["total_ms"])
-        trials.append(dict(opts=c, ms=ms))
-        if verbose:
-            print(f"autotune {key}: {c} -> {ms:.1f} ms", flush=True)
-        if ms < best_ms:
-            best, best_ms = c, ms
+    fixed = fixed_opts(sim, with_mlp)
+    timed: Dict[str, float] = {}
+    trials = []
+
+    def time_of(opts: Dict) -> float:
+        k = json.dumps(opts, sort_keys=True)
+        if k not in timed:
+            ms = float("inf")
+            for _ in range(repeats):
+                sim.run(**opts)
+                ms = min(ms, sim.stats()["total_ms"])
+            timed[k] = ms
+            trials.append(dict(opts=opts, ms=ms))
+            if verbose:
+                print(f"autotune {key}: {opts} -> {ms:.1f} ms", flush=True)
+        return timed[k]
+
+    best = dict(BASE, **fixed)
+    best_ms = time_of(best)
+    for _ in range(passes):
+        for name, values in (knobs or KNOBS):
+            for v in values:
+                cand = dict(best, **{name: v})
+                ms = time_of(cand)
+                if ms < best_ms:
+                    best, best_ms = cand, ms
     if use_cache:
+        cache = _load_cache(cache_path)
         cache[key] = dict(opts=best, ms=best_ms, trials=trials)
         tmp = cache_path + f".{os.getpid()}.tmp"
         with open(tmp, "w") as fh:

@@ -114,6 +114,8 @@ struct rtlfs_ctx {
     std::vector<uint64_t> graph_key;
     uint32_t graph_launches = 0;
     cudaEvent_t ev_graph[2] = {};
+    cudaEvent_t ev_gend = nullptr;   // end of the good-trace stream (timed inside a graph)
+    DBuf<uint32_t> d_gdone;          // nonzero once a windowed campaign's good trace is done
     // pinned scratch: [0..7] queue heads/counters, [8..9] heavy counts, [10..11] counter init
     unsigned long long *p_small = nullptr;
     int n_sm = 0;
@@ -874,7 +876,10 @@ int ensure_mlp(rtlfs_ctx *ctx) {
 
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        (void)cudaGetLastError();   // not sticky: keep it from reaching a later launch check
+        return 0.f;
+    }
     return ms;
 }
 
@@ -1079,6 +1084,8 @@ int rtlfs_create(rtlfs_ctx **out, int device) {
         CU(cudaEventCreateWithFlags(&ctx->ev_wl, cudaEventDisableTiming));
         for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
         for (auto &e : ctx->ev_graph) CU(cudaEventCreate(&e));
+        CU(cudaEventCreate(&ctx->ev_gend));
+        CU(ctx->d_gdone.reserve(1));
         CU(ctx->d_counters.reserve(4));
         CU(ctx->d_heads.reserve(8));
         CU(cudaMallocHost(&ctx->p_small, 16 * sizeof(unsigned long long)));
@@ -1099,6 +1106,7 @@ void rtlfs_destroy(rtlfs_ctx *ctx) {
     ctx->designs.clear();
     for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
     for (auto &e : ctx->ev_graph) if (e) cudaEventDestroy(e);
+    if (ctx->ev_gend) cudaEventDestroy(ctx->ev_gend);
     for (auto &e : ctx->ev_win) if (e) cudaEventDestroy(e);
     if (ctx->ev_wg) cudaEventDestroy(ctx->ev_wg);
     if (ctx->ev_wl) cudaEventDestroy(ctx->ev_wl);
@@ -1222,6 +1230,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         return fail(ctx, RTLFS_E_ARG, "good_cluster must be 0, 1, 2, 4, 8 or 16");
     ctx->good_cluster = (uint32_t)o.good_cluster;
     if (o.good_staging < 0 || o.good_staging > 1) return fail(ctx, RTLFS_E_ARG, "good_staging must be 0 or 1");
+    if (o.good_reserve < 0 || o.good_reserve > 1024) return fail(ctx, RTLFS_E_ARG, "good_reserve must be 0..1024");
     ctx->good_staging = (uint32_t)o.good_staging;
     CU(cudaSetDevice(ctx->device));
     const auto t_host0 = std::chrono::steady_clock::now();
@@ -1275,7 +1284,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     qi.counters = ctx->d_heads.p + 6;
     Queues qp = ql;
     qp.counters = ctx->d_heads.p + 6;
-    const int per_sm = light_max_blocks_per_sm(lcap, lblock);
+    const int per_sm = light_max_blocks_per_sm(lcap, lblock, o.window > 0);
     if (per_sm < 1) return fail(ctx, RTLFS_E_ARG, "light kernel cannot be resident");
     const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((ql.n_light + lblock - 1) / lblock,
                                                                    (int64_t)per_sm * ctx->n_sm));
@@ -1307,7 +1316,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(ctx->w_pool_v0.reserve(pool_cap));
         CU(ctx->w_pool_v1.reserve(pool_cap));
         ctx->w_pool_cap = pool_cap;
-        CU(ctx->w_cnt32.reserve(3 * (size_t)nw + 4));   // n_live, prom_end, n_carry | prom_total, n_light, zero
+        CU(ctx->w_cnt32.reserve(5 * (size_t)nw + 4));   // n_live, prom_end, n_carry | prom_total, n_light, zero | light, heavy CTAs that left
         CU(ctx->w_cnt64.reserve(3 * (size_t)nw + 1));   // pool_top, light head, heavy head
         while (ctx->ev_win.size() < 4 * (size_t)nw) {
             cudaEvent_t e;
@@ -1336,7 +1345,14 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         if (w_begin >= w_end) return fail(ctx, RTLFS_E_ARG, "stop_cycle is not after the checkpoint");
         if (ctx->ck.pool_r.size() > ctx->w_pool_cap) return fail(ctx, RTLFS_E_ARG, "checkpoint pool exceeds capacity");
     }
-    const bool timed_windows = W && !o.use_graph;
+    // Per-window kernel times: plain event records, or, while the campaign is captured into
+    // a graph, event-record nodes of the graph itself (external records), which keep their
+    // timestamps on every replay.
+    const bool timed_windows = W != 0;
+    const uint32_t reserve = W ? (uint32_t)o.good_reserve : 0u;
+    auto rec_time = [&](cudaEvent_t e, cudaStream_t s) -> cudaError_t {
+        return o.use_graph ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+    };
     // Activation bitplane: built after the good trace (per window when windows are whole
     // multiples of 64 cycles); otherwise the kernels scan the good trace.
     const bool use_act = F > 0 && (W == 0 || W % 64 == 0);
@@ -1361,10 +1377,11 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             CU(cudaMemsetAsync(ctx->d_cycle.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->d_port.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
         }
-        CU(cudaMemsetAsync(c32, 0, (3 * (size_t)nw + 4) * sizeof(uint32_t), ctx->s_main));
+        CU(cudaMemsetAsync(c32, 0, (5 * (size_t)nw + 4) * sizeof(uint32_t), ctx->s_main));
         CU(cudaMemsetAsync(c64, 0, (3 * (size_t)nw + 1) * sizeof(unsigned long long), ctx->s_main));
         CU(cudaMemcpyAsync(prom_total, ctx->p_small + 10, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
+        if (reserve) CU(cudaMemsetAsync(ctx->d_gdone.p, 0, sizeof(uint32_t), ctx->s_main));
         if (F && !resuming) {
             CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->w_st_nreg.p, 0, F, ctx->s_main));
@@ -1378,22 +1395,29 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(cudaStreamWaitEvent(ctx->s_heavy, ctx->ev_wl, 0));
         const uint32_t lblocks = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(((int64_t)F + lblock - 1) / lblock,
                                                                                   (int64_t)lgrid_cap));
+        // The scheduler of the first window reads the toggle rates of the first TOGGLE_CYCLES
+        // cycles, so the good trace runs that far ahead before the first light kernel.
+        const uint32_t w_sched = dev_sched && w_begin == 0 ? (std::min(TOGGLE_CYCLES, Tmax) + W - 1) / W : 0;
+        uint32_t g_next = w_begin;   // next window whose good trace is to be enqueued
         for (uint32_t w = w_begin; w < w_end; ++w) {
             const uint32_t t0 = w * W, t1 = std::min(t0 + W, Tmax);
-            // good trace of the window
-            int r3 = launch_good_lists(ctx, ctx->s_good, t0, t1, &launches);
-            if (r3 != RTLFS_OK) return r3;
-            CU(launch_transpose_window(ctx->d_designs.p, (uint32_t)ctx->designs.size(), max_net, t0, t1, ctx->s_good));
-            ++launches;
-            if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, t0, t1, ctx->s_good)); ++launches; }
-            if (w == w_begin) CU(cudaEventRecord(ev[1], ctx->s_good));
+            // good trace of the window (and of the windows the scheduler needs)
+            for (; g_next <= std::max(w, w_sched ? w_sched - 1 : 0u) && g_next < nw; ++g_next) {
+                const uint32_t g0 = g_next * W, g1 = std::min(g0 + W, Tmax);
+                int r3 = launch_good_lists(ctx, ctx->s_good, g0, g1, &launches);
+                if (r3 != RTLFS_OK) return r3;
+                CU(launch_transpose_window(ctx->d_designs.p, (uint32_t)ctx->designs.size(), max_net, g0, g1, ctx->s_good));
+                ++launches;
+                if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, g0, g1, ctx->s_good)); ++launches; }
+                if (g_next == w_begin) CU(cudaEventRecord(ev[1], ctx->s_good));
+            }
             CU(cudaEventRecord(ctx->ev_wg, ctx->s_good));
             // light kernel of the window (after the scheduler for the first one)
             CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_wg, 0));
             if (w == 0) {
                 if (dev_sched) {
                     CU(launch_features(ctx->d_designs.p, f, ctx->d_static_ptrs.p, ctx->d_X.p, ctx->d_heur.p,
-                                       ctx->s_main, t1));
+                                       ctx->s_main, TOGGLE_CYCLES));
                     const float *score = ctx->d_heur.p;
                     if (use_mlp) {
                         CU(launch_mlp_forward(ctx->d_wb.p, ctx->d_X.p, F, ctx->d_pred.p, ctx->s_main));
@@ -1425,9 +1449,12 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             wl.budget_hit = ctx->d_heads.p + 3;
             wl.fault_budget = o.fault_budget;
             wl.counters = ctx->d_heads.p + 4;
-            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[0 * nw + w], ctx->s_main));
+            wl.reserve_sm = reserve;
+            wl.good_done = ctx->d_gdone.p;
+            wl.n_left = c32 + 3 * nw + 4 + w;
+            if (timed_windows) CU(rec_time(ctx->ev_win[0 * nw + w], ctx->s_main));
             if (F) { CU(launch_light_window(ctx->d_designs.p, f, wl, lcap, lblock, (int)lblocks, ctx->s_main)); ++launches; }
-            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[1 * nw + w], ctx->s_main));
+            if (timed_windows) CU(rec_time(ctx->ev_win[1 * nw + w], ctx->s_main));
             CU(cudaMemcpyAsync(c32 + nw + w, prom_total, sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->s_main));
             CU(cudaEventRecord(ctx->ev_wl, ctx->s_main));
             // heavy kernel of the window: carried heavy faults plus this window's promotions
@@ -1453,12 +1480,17 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             wh.fault_budget = o.fault_budget;
             wh.counters = ctx->d_heads.p + 6;
             wh.err = ctx->d_err.p;
-            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[2 * nw + w], ctx->s_heavy));
+            wh.reserve_sm = reserve;
+            wh.good_done = ctx->d_gdone.p;
+            wh.n_left = c32 + 4 * nw + 4 + w;
+            if (timed_windows) CU(rec_time(ctx->ev_win[2 * nw + w], ctx->s_heavy));
             CU(launch_heavy_window(ctx->d_designs.p, f, wh, hs, hblock, hgrid, ctx->s_heavy));
             ++launches;
-            if (timed_windows) CU(cudaEventRecord(ctx->ev_win[3 * nw + w], ctx->s_heavy));
+            if (timed_windows) CU(rec_time(ctx->ev_win[3 * nw + w], ctx->s_heavy));
         }
         CU(cudaEventRecord(ev[2], ctx->s_main));
+        if (reserve) CU(cudaMemsetAsync(ctx->d_gdone.p, 1, 1, ctx->s_good));   // the reserved SMs are free again
+        if (o.use_graph) CU(rec_time(ctx->ev_gend, ctx->s_good));
         CU(cudaEventRecord(ev[3], ctx->s_good));
         CU(cudaStreamWaitEvent(ctx->s_main, ev[3], 0));
         CU(cudaEventRecord(ev[4], ctx->s_heavy));
@@ -1537,7 +1569,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         std::vector<uint64_t> key = {F, n_heavy, ql.n_light, (uint64_t)lcap, (uint64_t)lblock,
                                      (uint64_t)lgrid, (uint64_t)hblock, (uint64_t)hgrid,
                                      (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W,
-                                     (uint64_t)nodrop};
+                                     (uint64_t)nodrop, (uint64_t)reserve};
         const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p, ctx->h_gbm.p,
                               ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
                               ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,
@@ -1548,7 +1580,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                               ctx->w_st_v.p, ctx->w_live0.p, ctx->w_live1.p, ctx->w_cnt32.p, ctx->w_cnt64.p,
                               ctx->w_carry0.p, ctx->w_carry1.p, ctx->w_pool_r0.p, ctx->w_pool_r1.p,
                               ctx->d_fport.p, ctx->d_ft0.p, ctx->d_mism.p,
-                              ctx->w_pool_v0.p, ctx->w_pool_v1.p, ctx->d_act.p};
+                              ctx->w_pool_v0.p, ctx->w_pool_v1.p, ctx->d_act.p, ctx->d_gdone.p};
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,
@@ -1606,7 +1638,15 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     // Scatter results and counters.
     rtlfs_stats &st = ctx->stats;
     st = rtlfs_stats{};
-    if (o.use_graph) {   // whole campaign only; per-phase times are not available
+    if (o.use_graph && W) {   // whole campaign, good-trace stream and each window kernel
+        st.total_ms = ev_ms(ctx->ev_graph[0], ctx->ev_graph[1]);
+        st.good_ms = ev_ms(ctx->ev_graph[0], ctx->ev_gend);
+        st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
+        for (uint32_t w = w_begin; w < w_end; ++w) {
+            st.light_ms += ev_ms(ctx->ev_win[w], ctx->ev_win[nw + w]);
+            st.heavy_ms += ev_ms(ctx->ev_win[2 * nw + w], ctx->ev_win[3 * nw + w]);
+        }
+    } else if (o.use_graph) {   // whole campaign only; per-phase times are not available
         st.total_ms = ev_ms(ctx->ev_graph[0], ctx->ev_graph[1]);
         st.prep_ms = std::chrono::duration<double, std::milli>(t_host1 - t_host0).count();
     } else if (W) {   // overlapped phases: each kernel's own summed duration

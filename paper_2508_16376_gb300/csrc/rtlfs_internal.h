@@ -193,6 +193,9 @@ struct WinLight {
     unsigned long long *budget_hit;
     uint64_t fault_budget;
     unsigned long long *counters; // [0] evaluations, [1] fault-cycles
+    uint32_t reserve_sm;          // CTAs on SMs below this id leave while *good_done == 0
+    const uint32_t *good_done;    // nonzero once the last window's good trace is done
+    uint32_t *n_left;             // CTAs of this launch that left (zero before it)
 };
 
 struct WinHeavy {
@@ -215,6 +218,9 @@ struct WinHeavy {
     uint64_t fault_budget;
     unsigned long long *counters;
     uint32_t *err;                // bit 1: pool overflow
+    uint32_t reserve_sm;          // CTAs on SMs below this id leave while *good_done == 0
+    const uint32_t *good_done;    // nonzero once the last window's good trace is done
+    uint32_t *n_left;             // CTAs of this launch that left (zero before it)
 };
 
 // Launchers (rtlfs_kernels.cu). All enqueue on `stream` and return the launch status.
@@ -259,7 +265,8 @@ cudaError_t launch_plain(const DevDesign *d_designs, uint32_t design, DevFaults 
                          uint32_t *qstamp, uint32_t *heap, uint32_t *reg_r, uint64_t *reg_v,
                          uint32_t stride_net, uint32_t stride_node, uint32_t stride_reg,
                          cudaStream_t stream);
-int light_max_blocks_per_sm(int cap, int block);
+// Resident CTAs per SM of the light kernel (the windowed form's when `window`).
+int light_max_blocks_per_sm(int cap, int block, bool window);
 int heavy_max_blocks_per_sm(int block, size_t smem, bool exact, bool gbm);
 
 }  // namespace rtlfs

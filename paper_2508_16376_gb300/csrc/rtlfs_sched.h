@@ -14,10 +14,12 @@ constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;          // 4544
 constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;          // 4608
 constexpr int MLP_PARAMS = MLP_OFF_B3 + 1;              // 4609
 constexpr uint32_t SORT_BUCKETS = 4096;
+// Cycles the toggle-rate feature is measured over: the first min(T, TOGGLE_CYCLES).
+constexpr uint32_t TOGGLE_CYCLES = 256;
 
 // Toggle rates are measured over the first min(T, t_limit) cycles of each design.
 cudaError_t launch_features(const DevDesign *d_designs, DevFaults f, const float *const *net_static,
-                            float *X, float *heur, cudaStream_t s, uint32_t t_limit = 0xFFFFFFFFu);
+                            float *X, float *heur, cudaStream_t s, uint32_t t_limit = TOGGLE_CYCLES);
 cudaError_t launch_mlp_forward(const void *wb, const float *X, uint32_t n, float *y, cudaStream_t s);
 size_t mlp_grad_smem();
 cudaError_t launch_mlp_grad(const void *wb, const float *X, const float *t, uint32_t n, float *grad,

@@ -2,13 +2,12 @@
 // one-thread-per-fault kernel whose per-thread scratch lives in one file-scope device
 // array instead of memory obtained from cudaMalloc.
 //
-// Who needs it: code that must not allocate device memory at the point where it runs --
-// work issued while a CUDA stream is being captured into a graph (cudaMalloc is not a
-// stream operation and breaks the capture), latency-critical paths that cannot afford an
-// allocation or a possible implicit synchronisation, and hosts whose device memory is
-// owned by another allocator (a framework's caching pool) that this library cannot call.
-// Such a caller passes its own device buffers for the faults and the results; the design
-// and its good trace come from a context that was set up earlier.
+// Who needs it: callers that cannot obtain device memory from cudaMalloc where they run --
+// a process whose device memory is owned by another allocator (a framework's caching pool
+// that has reserved the GPU, which this library cannot call into), and latency-critical
+// paths that cannot afford an allocation or the device-wide synchronisation cudaMalloc
+// and cudaFree can imply. Such a caller passes its own device buffers for the faults and
+// the results; the design and its good trace come from a context that was set up earlier.
 //
 // The array below is part of the library image: every GPU that loads the library keeps
 // its 64 MiB until the process exits. Every call shares it, it keeps the contents the last

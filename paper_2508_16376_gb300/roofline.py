@@ -1,78 +1,143 @@
-"""Roofline accounting of the campaign's kernels from the library's own counters.
+"""Roofline accounting of a campaign step from its algorithmic counts.
 
-Algorithmic bytes per unit of work (what the method reads or writes by construction,
-counting every access once and assuming no reuse across faults or cycles):
+The path has no dense contraction, so the two roofs are HBM bandwidth and the integer
+ALU issue rate. Both numerators are algorithmic: what the method must move or compute by
+construction, independent of how the kernels happen to do it.
 
-* good-trace kernel, per simulated cycle of a design: every net's good value is written
-  once (8 B per net) plus the cycle's input vector read (8 B per input);
-* light kernel: per fault-cycle it simulates, the site's good value (8 B, the activation
-  check); per node evaluation, the node descriptor (16 B), its net record (16 B), the
-  node's good value (8 B) and two operand values (16 B) -- 56 B;
-* heavy kernel: per node evaluation the same 56 B plus the stamp reads of the two operands
-  (8 B) and the stamp+value write of a kept net (12 B) -- 76 B; per fault-cycle 8 B.
+HBM bytes per step:
+* the good trace, written once and read once: 2 x 8 B x nets x cycles per design (net
+  values are stored as 64-bit words);
+* the stimulus read once: 8 B x inputs x cycles;
+* the per-fault state carried across cycle-window boundaries: every fault still alive at a
+  boundary writes and reads its live-list entry (4 B) and register-diff count (1 B), 10 B
+  per crossing (the register-diff entries themselves are not counted: the library's
+  counters do not record them);
+* the fault descriptors read (8 B) and the results (cycle, port, detected: 9 B) and loads
+  (8 B) written once per fault.
 
-The peak is the measured HBM copy bandwidth (MEASURED_PEAKS.json, burst figure); the
-fraction is achieved / peak. These kernels are bound by dependent-load latency per fault
-rather than by either roof, which the small fractions show.
+Integer operations per step, from the fixed table OPS of 32-bit integer instructions per
+op for a result of at most 32 bits / more than 32 bits (a 64-bit value takes two 32-bit
+words), plus the width mask (MASK) and, for a faulty evaluation, the compare with the good
+value that decides whether the net is kept (KEEP):
+* good machine: every node once per cycle, OPS + MASK;
+* faulty machines: the recorded node evaluations times the mean of OPS + MASK + KEEP over
+  the designs' nodes (the counters record evaluations, not their op mix);
+* one output check per simulated fault-cycle.
+
+Peaks: HBM from MEASURED_PEAKS.json (a measured copy); the integer peak is derived as SMs x
+INT32 lanes per SM x the SM clock sampled during the timed region. The lane count is the
+one a throughput probe measured on a GB300 (independent add/xor chains: 64 results per SM
+per clock).
 """
 from __future__ import annotations
 
-import hashlib
-import os
-from typing import Optional
+from typing import Dict, List, Optional
 
-LIGHT_BYTES_PER_EVAL = 56
-LIGHT_BYTES_PER_FAULT_CYCLE = 8
-HEAVY_BYTES_PER_EVAL = 76
-HEAVY_BYTES_PER_FAULT_CYCLE = 8
+import numpy as np
+
+from . import synth as _s
+
 FALLBACK_HBM_GBS = 6800.0
+N_SM = 152
+INT32_LANES_PER_SM = 64
 
-# DRAM bytes (read + write) per window launch of 256 cycles, measured with ncu on the medium
-# workload's first 1024 cycles (a full-size launch covers the same window and faults); valid
-# only for the kernel source they were measured on, identified by its hash.
-MEASURED_TRAFFIC = {"light": 59.78e6, "heavy": 117.21e6, "good_trace": 0.76e6}
-MEASURED_SOURCE_SHA256_PREFIX = "48bd56eee94319b8"
-KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "rtlfs_kernels.cu")
-
-
-def measured_traffic(window: int) -> Optional[dict]:
-    """Per-launch DRAM traffic of the window kernels, or None when the kernel source has
-    changed since the capture or the window is not the captured one."""
-    if window != 256:
-        return None
-    try:
-        with open(KERNEL_SOURCE, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
-    except OSError:
-        return None
-    return dict(MEASURED_TRAFFIC) if sha.startswith(MEASURED_SOURCE_SHA256_PREFIX) else None
+OPS = {_s.AND: (1, 2), _s.OR: (1, 2), _s.XOR: (1, 2), _s.NOT: (1, 2), _s.ADD: (1, 2),
+       _s.SUB: (1, 2), _s.MUX2: (2, 3), _s.EQ: (1, 2), _s.LT: (1, 2), _s.SHL: (1, 2),
+       _s.SHR: (1, 2), _s.SLICE: (1, 2), _s.CONCAT: (2, 4), _s.CONST: (0, 0)}
+MASK = (1, 2)
+KEEP = (1, 2)
+SPILL_BYTES_PER_CROSSING = 10
+FAULT_BYTES = 8 + 9 + 8
 
 
-def kernel_bytes(stats: dict, design, T: int) -> dict:
-    good = design.n_net * T * 8 + design.n_in * T * 8
-    light = (stats["light_evals"] * LIGHT_BYTES_PER_EVAL
-             + stats["light_fault_cycles"] * LIGHT_BYTES_PER_FAULT_CYCLE)
-    heavy = (stats["heavy_evals"] * HEAVY_BYTES_PER_EVAL
-             + stats["heavy_fault_cycles"] * HEAVY_BYTES_PER_FAULT_CYCLE)
-    return {"good_trace": good, "light": light, "heavy": heavy}
+def windows(run_opts: dict, T: int) -> int:
+    """Launches of each window kernel per campaign."""
+    W = int(run_opts.get("window", 0) or 0)
+    return -(-int(T) // W) if W else 1
 
 
-def kernel_ms(stats: dict) -> dict:
-    return {"good_trace": stats["good_ms"], "light": stats["light_ms"], "heavy": stats["heavy_ms"]}
+def node_ops(design) -> tuple:
+    """(good-machine ops per cycle, sum over nodes of the faulty evaluation's ops)."""
+    op = np.asarray(design.node_op, np.int64)
+    wide = (np.asarray(design.node_w, np.int64) > 32).astype(np.int64)
+    table = np.array([OPS[k] for k in range(len(OPS))], np.int64)
+    base = table[op, wide] + np.array(MASK)[wide]
+    return int(base.sum()), int((base + np.array(KEEP)[wide]).sum())
 
 
-def dominant_roofline(stats: dict, peaks: dict, design, T: int, launches: int = 1,
-                      traffic: Optional[dict] = None) -> dict:
-    """Roofline entry for the kernel with the largest share of the campaign time. `launches`
-    = launches of each window kernel per campaign; achieved = algorithmic bytes per launch /
-    average launch duration (the same ratio as the totals); traffic = DRAM bytes per launch."""
-    ms = kernel_ms(stats)
-    name = max(ms, key=lambda k: ms[k])
-    by = kernel_bytes(stats, design, T)
+def crossings(parts, results, W: int) -> int:
+    """Window boundaries crossed by live faults: sum over faults of ceil(c / W) - 1, c the
+    cycles simulated (first detection + 1, or T)."""
+    if not W or results is None:
+        return 0
+    n = 0
+    for (d, stim, f), r in zip(parts, results):
+        det, cyc = np.asarray(r[0]), np.asarray(r[1], np.int64)
+        c = np.where(det == 1, cyc + 1, stim.shape[0])
+        n += int(np.sum(np.maximum(-(-c // W) - 1, 0)))
+    return n
+
+
+def step_bytes(parts, results, run_opts: dict) -> Dict[str, int]:
+    trace = sum(2 * 8 * d.n_net * s.shape[0] for d, s, _ in parts)
+    stim = sum(8 * d.n_in * s.shape[0] for d, s, _ in parts)
+    spill = SPILL_BYTES_PER_CROSSING * crossings(parts, results, int(run_opts.get("window", 0) or 0))
+    faults = FAULT_BYTES * sum(len(f) for _, _, f in parts)
+    return {"good_trace": trace, "stimulus": stim, "window_state": spill, "faults": faults,
+            "total": trace + stim + spill + faults}
+
+
+def step_int_ops(parts, stats: dict) -> Dict[str, int]:
+    good = 0
+    s_eval, n_nodes = 0, 0
+    for d, s, _ in parts:
+        g, e = node_ops(d)
+        good += g * s.shape[0]
+        s_eval += e
+        n_nodes += d.n_node
+    faulty = int(stats["node_evals"] * (s_eval / max(n_nodes, 1)))
+    check = int(stats["fault_cycles"])
+    return {"good": good, "faulty": faulty, "output_check": check, "total": good + faulty + check}
+
+
+def int_peak(peaks: dict, sm_mhz: Optional[float], n_sm: int = N_SM) -> dict:
+    mhz = float(sm_mhz or peaks.get("sm_max_mhz") or 2070.0)
+    return {"tops": n_sm * INT32_LANES_PER_SM * mhz * 1e6 / 1e12, "n_sm": n_sm,
+            "lanes_per_sm": INT32_LANES_PER_SM, "sm_mhz": mhz}
+
+
+def _dominant(mean_ms: dict):
+    name = max(mean_ms, key=lambda k: mean_ms[k])
+    return {"good_ms": "good_trace", "light_ms": "light", "heavy_ms": "heavy"}[name], mean_ms[name]
+
+
+def step_roofline(parts, results, stats: dict, mean_ms: dict, run_opts: dict, peaks: dict,
+                  n_win: int, step_ms: float, ints: dict, traffic: Optional[float] = None) -> dict:
+    """HBM roofline: the step's algorithmic bytes over the dominant kernel's time (its
+    launches summed; per launch the same ratio), and over the whole step."""
+    by = step_bytes(parts, results, run_opts)
+    name, ms = _dominant(mean_ms)
     peak = float(peaks.get("hbm_gbs") or FALLBACK_HBM_GBS)
-    n = max(int(launches), 1)
-    achieved = (by[name] / n) / (ms[name] / n / 1000.0) / 1e9 if ms[name] > 0 else 0.0
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
-            "algorithmic_bytes_per_launch": int(by[name] / n), "launches": n,
-            "avg_launch_ms": ms[name] / n, "traffic": (traffic or {}).get(name)}
+    ach = by["total"] / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+    step = by["total"] / (step_ms / 1000.0) / 1e9 if step_ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+            "algorithmic_bytes_per_step": by["total"], "bytes": by,
+            "algorithmic_bytes_per_launch": by["total"] // max(n_win, 1), "launches": n_win,
+            "avg_launch_ms": ms / max(n_win, 1), "kernel_ms_per_step": ms,
+            "step_achieved": step, "step_frac": step / peak, "traffic": traffic}
+
+
+def step_alu(parts, stats: dict, mean_ms: dict, n_win: int, step_ms: float, ints: dict) -> dict:
+    """Integer-ALU roofline: the step's algorithmic 32-bit integer operations over the
+    dominant kernel's time and over the whole step, against SMs x lanes x clock."""
+    ops = step_int_ops(parts, stats)
+    name, ms = _dominant(mean_ms)
+    peak = ints["tops"]
+    ach = ops["total"] / (ms / 1000.0) / 1e12 if ms > 0 else 0.0
+    step = ops["total"] / (step_ms / 1000.0) / 1e12 if step_ms > 0 else 0.0
+    return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "Tops/s",
+            "frac": ach / peak, "peak_source": f"derived: {ints['n_sm']} SMs x {ints['lanes_per_sm']} "
+                                               f"INT32 lanes x {ints['sm_mhz']:.0f} MHz (sampled)",
+            "int_ops_per_step": ops["total"], "ops": ops, "launches": n_win,
+            "step_achieved": step, "step_frac": step / peak}

@@ -14,11 +14,11 @@ Which faults are checked:
   batch   the 64-design batch: the same rule per design.
 The strata are structural (read from the design's arrays), never taken from a GPU run.
 
-  python tests/golden/fullsize_golden.py {medium,large,batch} [--part K/N] [--threads T]
+  python tests/golden/fullsize_golden.py {medium,large,batch} [--part K[-L]/N] [--threads T]
                                           [--deadline SECONDS] [--out DIR]
 
 A part K/N takes every N-th selected fault starting at K (a uniform sample of the
-selection); with a deadline the script stops taking new faults when it expires and stores
+selection; K-L/N takes parts K..L); with a deadline the script stops taking new faults when it expires and stores
 the ones it finished. The tests read every part file of a workload and check the union.
 """
 from __future__ import annotations
@@ -134,13 +134,16 @@ def main() -> int:
     args = ap.parse_args()
     import oracle
     oracle.build()
-    k, n = (int(x) for x in args.part.split("/"))
+    ks, n = args.part.split("/")
+    n = int(n)
+    lo, _, hi = ks.partition("-")
+    parts = list(range(int(lo), int(hi or lo) + 1))
     t_start = time.time()
     todo = []   # (design index, fault indices of one chunk)
     ctx = {}
     stored = load(args.name) if os.path.abspath(args.out) == DIR else {}
     for di, d, stim, f, sel in cases(args.name):
-        mine = sel[k::n]
+        mine = np.sort(np.concatenate([sel[k::n] for k in parts]))
         if di in stored:   # faults an earlier run already stored
             mine = mine[~np.isin(mine, stored[di][1])]
         if not len(mine):
@@ -150,7 +153,7 @@ def main() -> int:
         chunk = 1 if d.n_net > 100000 else 4
         todo += [(di, mine[i:i + chunk]) for i in range(0, len(mine), chunk)]
     fps = [ctx[i][4] if i in ctx else "" for i in range(max(ctx) + 1)] if ctx else []
-    print(f"{args.name} part {k}/{n}: {sum(len(c) for _, c in todo)} faults in {len(todo)} "
+    print(f"{args.name} parts {parts} of {n}: {sum(len(c) for _, c in todo)} faults in {len(todo)} "
           f"chunks, good runs {time.time() - t_start:.1f} s", flush=True)
     done = []
     lock = threading.Lock()
@@ -183,7 +186,7 @@ def main() -> int:
                 port=np.concatenate([x[4] for x in done]).astype(np.int32),
                 fingerprints=np.array(fps))
     os.makedirs(args.out, exist_ok=True)
-    tag = f"p{k:02d}of{n:02d}"
+    tag = f"p{parts[0]:02d}-{parts[-1]:02d}of{n:02d}"
     path = os.path.join(args.out, f"{args.name}_{tag}.npz")
     if os.path.exists(path):   # a part cut short by its deadline: keep both files
         path = os.path.join(args.out, f"{args.name}_{tag}_{int(time.time())}.npz")

@@ -40,7 +40,7 @@ def test_struct_sizes_match_header():
     assert rtlfs.FAULT_DTYPE.itemsize == 8
     assert rtlfs.RESULT_DTYPE.itemsize == 12
     assert rtlfs.FAULT_EX_DTYPE.itemsize == 16
-    assert ctypes.sizeof(rtlfs.rtlfs_run_opts) == 4 * 6 + 8 + 32
+    assert ctypes.sizeof(rtlfs.rtlfs_run_opts) == 4 * 6 + 8 + 36 + 4   # + tail padding to 8
     assert ctypes.sizeof(rtlfs.rtlfs_stats) == 6 * 8 + 4 * 8 + 8 + 4 * 8
 
 

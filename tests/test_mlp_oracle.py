@@ -91,3 +91,17 @@ def test_counter_features_by_hand():
         [0.0, 2 / 2, 1.0, 4 / 64, 9 / 19],
     ])
     assert np.allclose(X, exp, atol=1e-12), X
+
+
+def test_toggle_rate_uses_the_first_256_cycles():
+    """Counter over T = 300 cycles: the toggle rate counts changes over t = 1..255 only (the
+    prefix a campaign has when it orders its first window). Q bit 0 changes every cycle:
+    255 / 255. Q bit 3 (Q_t = t mod 16) changes when t is a multiple of 8: 31 times in
+    1..255 -> 31 / 255 (over the whole stimulus it would be 37 / 299). s bit 0
+    (s_t = (t+1) mod 16) changes every cycle: 1."""
+    d = synth.counter4()
+    stim = np.zeros((300, 1), np.uint64)
+    _, trace = oracle.good_run(d, stim, with_trace=True)
+    f = synth.Faults(np.array([1, 1, 3], np.uint32), np.array([0, 3, 0], np.uint8), np.zeros(3, np.uint8))
+    X = mlp.features(d, trace, f)
+    assert np.allclose(X[:, 4], [1.0, 31 / 255, 1.0], atol=1e-12), X[:, 4]

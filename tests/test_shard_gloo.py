@@ -36,6 +36,46 @@ def _worker(rank, world, port, out_path):
     dist.destroy_process_group()
 
 
+def _campaign_worker(rank, world, port, out_path):
+    """bench.py's rank path on two designs: LPT shards of each design's list from the same
+    predicted loads, this rank's shards simulated (the oracle stands in for the GPU), and
+    gather_results assembling full-length results on every rank."""
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    parts = _two_designs()
+    pred = [np.random.default_rng(7 + i).uniform(0, 10, len(f)) for i, (_, _, f) in enumerate(parts)]
+    mine = [shard.lpt_shards(p, world)[rank] for p in pred]
+    res = [np.stack(oracle.fault_sim(d, s, f.take(m), threads=2)).astype(np.int64)
+           for (d, s, f), m in zip(parts, mine)]
+    full = shard.gather_results(res, mine, [len(f) for _, _, f in parts])
+    np.savez(out_path + f".{rank}.npz", *full)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _two_designs():
+    out = []
+    for seed in (1, 2):
+        d = synth.tiny_design(seed)
+        out.append((d, synth.stimulus(d, 80, 100 + seed), synth.sample_faults(d, 1500, seed)))
+    return out
+
+
+def test_two_rank_campaign_shards_gather_on_every_rank(tmp_path):
+    import oracle
+    oracle.build()
+    out = str(tmp_path / "camp")
+    mp.start_processes(_campaign_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    for rank in range(2):
+        r = np.load(out + f".{rank}.npz")
+        for i, (d, s, f) in enumerate(_two_designs()):
+            exp = np.stack(oracle.fault_sim(d, s, f, threads=4))
+            assert np.array_equal(r[f"arr_{i}"], exp)
+
+
 def test_two_rank_gloo_gather_equals_single_run(tmp_path):
     import oracle
     oracle.build()
