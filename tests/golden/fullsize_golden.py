@@ -141,7 +141,7 @@ def main() -> int:
     t_start = time.time()
     todo = []   # (design index, fault indices of one chunk)
     ctx = {}
-    stored = load(args.name) if os.path.abspath(args.out) == DIR else {}
+    stored = load(args.name)   # faults already stored under tests/golden/fullsize are skipped
     for di, d, stim, f, sel in cases(args.name):
         mine = np.sort(np.concatenate([sel[k::n] for k in parts]))
         if di in stored:   # faults an earlier run already stored
