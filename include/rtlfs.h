@@ -179,13 +179,12 @@ typedef struct {
                                 warp stages them into a shared-memory ring with bulk
                                 asynchronous copies (TMA) for the consumer threads. Same
                                 results; RTLFS_E_CUDA if a staging wait runs out */
-    int32_t  good_reserve;   /* windowed form: SMs kept free for the good trace while it is
-                                still running ahead of the faulty kernels. Until the last
-                                window's good trace is done, light and heavy CTAs that start
-                                on an SM whose id is below good_reserve leave at once (their
-                                faults go to the other CTAs through the work queues), so
-                                the good trace of later windows never waits for a window's
-                                faulty kernels to drain. 0 = none. Same results */
+    int32_t  good_first;     /* windowed form: 1 = the good trace of every cycle (one launch
+                                per design list), its transposition and the activation
+                                bitplane run before the first faulty window, so the faulty
+                                kernels never wait for the good trace; 0 = the good trace of
+                                window w+1 overlaps the faulty kernels of window w. Ignored
+                                by a run that stops at stop_cycle or resumes. Same results */
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */

@@ -2,7 +2,8 @@
 and heavy kernels; 0 = one pass over all cycles), the light-lane capacity, the fraction of
 faults the scheduler sends to the heavy kernel from cycle 0 (the light/heavy split), and
 the CTA sizes of the light kernel (lanes per CTA) and of the heavy kernel (threads per
-heavy fault), and the SMs kept free for the good trace while it runs ahead (good_reserve).
+heavy fault), and whether the whole good trace runs before the first faulty window
+(good_first) or window by window, overlapped with the faulty kernels.
 
 Every candidate is timed with real campaigns through rtlfs_run on the workload loaded in
 the simulator (device-event time of the whole campaign, best of `repeats`). The search is
@@ -23,14 +24,14 @@ from .rtlfs import SCHED_HEURISTIC, SCHED_MLP
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 
-BASE = dict(window=256, light_cap=1, heavy_frac=0.0, light_block=128, heavy_block=32, good_reserve=0)
+BASE = dict(window=256, light_cap=1, heavy_frac=0.0, light_block=128, heavy_block=32, good_first=0)
 KNOBS: List[Tuple[str, Sequence]] = [
     ("window", (256, 128, 512, 64, 0)),
     ("light_cap", (1, 2)),
     ("heavy_frac", (0.0, 0.02, 0.05)),
     ("light_block", (128, 64, 256)),
     ("heavy_block", (32, 64)),
-    ("good_reserve", (0, 32, 64)),
+    ("good_first", (0, 1)),
 ]
 
 

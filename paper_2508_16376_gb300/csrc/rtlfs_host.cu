@@ -115,7 +115,6 @@ struct rtlfs_ctx {
     uint32_t graph_launches = 0;
     cudaEvent_t ev_graph[2] = {};
     cudaEvent_t ev_gend = nullptr;   // end of the good-trace stream (timed inside a graph)
-    DBuf<uint32_t> d_gdone;          // nonzero once a windowed campaign's good trace is done
     // pinned scratch: [0..7] queue heads/counters, [8..9] heavy counts, [10..11] counter init
     unsigned long long *p_small = nullptr;
     int n_sm = 0;
@@ -1085,7 +1084,6 @@ int rtlfs_create(rtlfs_ctx **out, int device) {
         for (auto &e : ctx->ev) CU(cudaEventCreate(&e));
         for (auto &e : ctx->ev_graph) CU(cudaEventCreate(&e));
         CU(cudaEventCreate(&ctx->ev_gend));
-        CU(ctx->d_gdone.reserve(1));
         CU(ctx->d_counters.reserve(4));
         CU(ctx->d_heads.reserve(8));
         CU(cudaMallocHost(&ctx->p_small, 16 * sizeof(unsigned long long)));
@@ -1230,7 +1228,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         return fail(ctx, RTLFS_E_ARG, "good_cluster must be 0, 1, 2, 4, 8 or 16");
     ctx->good_cluster = (uint32_t)o.good_cluster;
     if (o.good_staging < 0 || o.good_staging > 1) return fail(ctx, RTLFS_E_ARG, "good_staging must be 0 or 1");
-    if (o.good_reserve < 0 || o.good_reserve > 1024) return fail(ctx, RTLFS_E_ARG, "good_reserve must be 0..1024");
+    if (o.good_first < 0 || o.good_first > 1) return fail(ctx, RTLFS_E_ARG, "good_first must be 0 or 1");
     ctx->good_staging = (uint32_t)o.good_staging;
     CU(cudaSetDevice(ctx->device));
     const auto t_host0 = std::chrono::steady_clock::now();
@@ -1316,7 +1314,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         CU(ctx->w_pool_v0.reserve(pool_cap));
         CU(ctx->w_pool_v1.reserve(pool_cap));
         ctx->w_pool_cap = pool_cap;
-        CU(ctx->w_cnt32.reserve(5 * (size_t)nw + 4));   // n_live, prom_end, n_carry | prom_total, n_light, zero | light, heavy CTAs that left
+        CU(ctx->w_cnt32.reserve(3 * (size_t)nw + 4));   // n_live, prom_end, n_carry | prom_total, n_light, zero
         CU(ctx->w_cnt64.reserve(3 * (size_t)nw + 1));   // pool_top, light head, heavy head
         while (ctx->ev_win.size() < 4 * (size_t)nw) {
             cudaEvent_t e;
@@ -1349,7 +1347,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     // a graph, event-record nodes of the graph itself (external records), which keep their
     // timestamps on every replay.
     const bool timed_windows = W != 0;
-    const uint32_t reserve = W ? (uint32_t)o.good_reserve : 0u;
+    const bool good_first = W && o.good_first && !stopping && !resuming;
     auto rec_time = [&](cudaEvent_t e, cudaStream_t s) -> cudaError_t {
         return o.use_graph ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
     };
@@ -1377,11 +1375,10 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             CU(cudaMemsetAsync(ctx->d_cycle.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->d_port.p, 0xFF, (size_t)F * sizeof(int32_t), ctx->s_main));
         }
-        CU(cudaMemsetAsync(c32, 0, (5 * (size_t)nw + 4) * sizeof(uint32_t), ctx->s_main));
+        CU(cudaMemsetAsync(c32, 0, (3 * (size_t)nw + 4) * sizeof(uint32_t), ctx->s_main));
         CU(cudaMemsetAsync(c64, 0, (3 * (size_t)nw + 1) * sizeof(unsigned long long), ctx->s_main));
         CU(cudaMemcpyAsync(prom_total, ctx->p_small + 10, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->s_main));
         CU(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(uint32_t), ctx->s_main));
-        if (reserve) CU(cudaMemsetAsync(ctx->d_gdone.p, 0, sizeof(uint32_t), ctx->s_main));
         if (F && !resuming) {
             CU(cudaMemsetAsync(ctx->d_load.p, 0, (size_t)F * sizeof(uint64_t), ctx->s_main));
             CU(cudaMemsetAsync(ctx->w_st_nreg.p, 0, F, ctx->s_main));
@@ -1399,6 +1396,17 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         // cycles, so the good trace runs that far ahead before the first light kernel.
         const uint32_t w_sched = dev_sched && w_begin == 0 ? (std::min(TOGGLE_CYCLES, Tmax) + W - 1) / W : 0;
         uint32_t g_next = w_begin;   // next window whose good trace is to be enqueued
+        if (good_first) {   // every cycle's good trace first: one launch per design list
+            int r3 = launch_good_lists(ctx, ctx->s_good, 0, Tmax, &launches);
+            if (r3 != RTLFS_OK) return r3;
+            for (Design *D : ctx->designs) {
+                CU(launch_transpose(D->d_gcol.p, D->d_rows.p, D->n_net, D->T, ctx->s_good));
+                ++launches;
+            }
+            if (use_act) { CU(launch_activation(ctx->d_designs.p, f, ctx->d_act.p, 0, Tmax, ctx->s_good)); ++launches; }
+            CU(cudaEventRecord(ev[1], ctx->s_good));
+            g_next = nw;
+        }
         for (uint32_t w = w_begin; w < w_end; ++w) {
             const uint32_t t0 = w * W, t1 = std::min(t0 + W, Tmax);
             // good trace of the window (and of the windows the scheduler needs)
@@ -1449,9 +1457,6 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             wl.budget_hit = ctx->d_heads.p + 3;
             wl.fault_budget = o.fault_budget;
             wl.counters = ctx->d_heads.p + 4;
-            wl.reserve_sm = reserve;
-            wl.good_done = ctx->d_gdone.p;
-            wl.n_left = c32 + 3 * nw + 4 + w;
             if (timed_windows) CU(rec_time(ctx->ev_win[0 * nw + w], ctx->s_main));
             if (F) { CU(launch_light_window(ctx->d_designs.p, f, wl, lcap, lblock, (int)lblocks, ctx->s_main)); ++launches; }
             if (timed_windows) CU(rec_time(ctx->ev_win[1 * nw + w], ctx->s_main));
@@ -1480,16 +1485,12 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             wh.fault_budget = o.fault_budget;
             wh.counters = ctx->d_heads.p + 6;
             wh.err = ctx->d_err.p;
-            wh.reserve_sm = reserve;
-            wh.good_done = ctx->d_gdone.p;
-            wh.n_left = c32 + 4 * nw + 4 + w;
             if (timed_windows) CU(rec_time(ctx->ev_win[2 * nw + w], ctx->s_heavy));
             CU(launch_heavy_window(ctx->d_designs.p, f, wh, hs, hblock, hgrid, ctx->s_heavy));
             ++launches;
             if (timed_windows) CU(rec_time(ctx->ev_win[3 * nw + w], ctx->s_heavy));
         }
         CU(cudaEventRecord(ev[2], ctx->s_main));
-        if (reserve) CU(cudaMemsetAsync(ctx->d_gdone.p, 1, 1, ctx->s_good));   // the reserved SMs are free again
         if (o.use_graph) CU(rec_time(ctx->ev_gend, ctx->s_good));
         CU(cudaEventRecord(ev[3], ctx->s_good));
         CU(cudaStreamWaitEvent(ctx->s_main, ev[3], 0));
@@ -1569,7 +1570,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         std::vector<uint64_t> key = {F, n_heavy, ql.n_light, (uint64_t)lcap, (uint64_t)lblock,
                                      (uint64_t)lgrid, (uint64_t)hblock, (uint64_t)hgrid,
                                      (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W,
-                                     (uint64_t)nodrop, (uint64_t)reserve};
+                                     (uint64_t)nodrop, (uint64_t)good_first};
         const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p, ctx->h_gbm.p,
                               ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
                               ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,
@@ -1580,7 +1581,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                               ctx->w_st_v.p, ctx->w_live0.p, ctx->w_live1.p, ctx->w_cnt32.p, ctx->w_cnt64.p,
                               ctx->w_carry0.p, ctx->w_carry1.p, ctx->w_pool_r0.p, ctx->w_pool_r1.p,
                               ctx->d_fport.p, ctx->d_ft0.p, ctx->d_mism.p,
-                              ctx->w_pool_v0.p, ctx->w_pool_v1.p, ctx->d_act.p, ctx->d_gdone.p};
+                              ctx->w_pool_v0.p, ctx->w_pool_v1.p, ctx->d_act.p};
         for (const void *q : ptrs) key.push_back((uint64_t)(uintptr_t)q);
         const GoodLaunch &g = ctx->gl;
         key.insert(key.end(), {g.n_smem, g.n_glob, g.max_net_s, g.max_reg_s, g.max_ch_s, g.max_ch_g,

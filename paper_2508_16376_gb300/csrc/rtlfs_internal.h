@@ -193,9 +193,6 @@ struct WinLight {
     unsigned long long *budget_hit;
     uint64_t fault_budget;
     unsigned long long *counters; // [0] evaluations, [1] fault-cycles
-    uint32_t reserve_sm;          // CTAs on SMs below this id leave while *good_done == 0
-    const uint32_t *good_done;    // nonzero once the last window's good trace is done
-    uint32_t *n_left;             // CTAs of this launch that left (zero before it)
 };
 
 struct WinHeavy {
@@ -218,9 +215,6 @@ struct WinHeavy {
     uint64_t fault_budget;
     unsigned long long *counters;
     uint32_t *err;                // bit 1: pool overflow
-    uint32_t reserve_sm;          // CTAs on SMs below this id leave while *good_done == 0
-    const uint32_t *good_done;    // nonzero once the last window's good trace is done
-    uint32_t *n_left;             // CTAs of this launch that left (zero before it)
 };
 
 // Launchers (rtlfs_kernels.cu). All enqueue on `stream` and return the launch status.

@@ -1377,29 +1377,9 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
 // Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
 // from the last window and those promoted in this one; survivors carry their register
 // diffs to the next window through the pool.
-// Whether this CTA leaves at once to keep its SM free for the good trace: it started on an
-// SM whose id is below `reserve` while the good trace has windows left, and it is not the
-// last CTA of the launch to decide so (one CTA always stays: the work queues are drained by
-// the CTAs that stay, so every fault is still simulated). Thread 0 decides for the whole
-// CTA (the flag may change while the threads read it).
-template <bool WARP>
-__device__ __forceinline__ bool leave_for_good_trace(uint32_t reserve, const uint32_t *good_done,
-                                                     uint32_t *n_left) {
-    __shared__ uint32_t s_leave;
-    if (threadIdx.x == 0) {
-        uint32_t sm;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
-        s_leave = sm < reserve && *(const volatile uint32_t *)good_done == 0u &&
-                  atomicAdd(n_left, 1u) + 1u < gridDim.x;
-    }
-    if (WARP) __syncwarp(); else __syncthreads();
-    return s_leave != 0u;
-}
-
 template <bool WARP, bool EXACT, bool GBM = false>
 __global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
 heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
-    if (q.reserve_sm && leave_for_good_trace<WARP>(q.reserve_sm, q.good_done, q.n_left)) return;
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
     __shared__ unsigned long long s_item, s_off;
@@ -1792,7 +1772,6 @@ light_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q) {
 template <int KR, int KD, int KH>
 __global__ void __launch_bounds__(256, 1)
 light_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinLight q) {
-    if (q.reserve_sm && leave_for_good_trace<false>(q.reserve_sm, q.good_done, q.n_left)) return;
     LIGHT_CARVE
     const Promote prom{q.prom, q.prom_total, q.prom_cap};
     const uint32_t n_live = *q.n_live_in;

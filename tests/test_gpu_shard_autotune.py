@@ -70,16 +70,17 @@ def test_autotuner_pick_is_oracle_exact(tmp_path):
         assert np.array_equal(np.stack(split(r)).astype(np.int64), e)
 
 
-@pytest.mark.parametrize("reserve", [8, 64, 151])
-def test_good_reserve_keeps_results(reserve):
-    """SMs kept free for the good trace (up to all but one): CTAs that leave hand their
-    faults to the others through the queues, and one CTA of every launch always stays."""
+@pytest.mark.parametrize("window", [64, 256])
+def test_good_first_keeps_results(window):
+    """The whole good trace before the first faulty window (one launch per design list,
+    transposes and activation bitplane over all cycles): the oracle's results, with and
+    without graph replay, with and without heavy pre-assignment."""
     parts = _small_batch()
     exp = _oracle(parts)
     with Simulator(0) as sim:
         for p in parts:
             sim.add(*p)
-        for g in (0, 1):
-            res, _ = sim.run(window=64, light_cap=1, good_reserve=reserve, use_graph=g, heavy_frac=0.05)
+        for g, hf in ((0, 0.0), (1, 0.05)):
+            res, _ = sim.run(window=window, light_cap=1, good_first=1, use_graph=g, heavy_frac=hf)
             for r, e in zip(res, exp):
-                assert np.array_equal(np.stack(split(r)).astype(np.int64), e), (reserve, g)
+                assert np.array_equal(np.stack(split(r)).astype(np.int64), e), (window, g)
