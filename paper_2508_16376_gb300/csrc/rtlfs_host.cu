@@ -152,7 +152,8 @@ struct rtlfs_ctx {
     DBuf<uint32_t> d_order;
     DBuf<HeavyItem> d_init_items, d_prom_items;
     DBuf<uint32_t> d_counters;        // [0] init count, [1] prom count
-    DBuf<uint32_t> d_err;             // bit 0: a good-trace staging wait ran out; bit 1: the heavy pool overflowed
+    DBuf<uint32_t> d_err;             // bit 0: a good-trace staging wait ran out; bit 1: the heavy pool overflowed;
+                                      // bit 2: a cluster good-trace launch ran without its clusters
     DBuf<unsigned long long> d_heads; // [0] light, [1] init heavy, [2] prom heavy, [3] budget,
                                       // [4..5] light evals/cycles, [6..7] heavy evals/cycles
     DBuf<HeavyVal> h_fval;
@@ -688,7 +689,7 @@ int launch_good_lists(rtlfs_ctx *ctx, cudaStream_t stream, uint32_t t0, uint32_t
     for (int lc = 1; lc < 5; ++lc) {
         if (!g.n_cl[lc]) continue;
         if (int r = next_stream(&st)) return r;
-        CU(launch_good_cluster(ctx->d_designs.p, ctx->d_list_cl[lc].p, g.n_cl[lc], 1u << lc, g.smem_cl[lc],
+        CU(launch_good_cluster(ctx->d_designs.p, ctx->d_list_cl[lc].p, g.n_cl[lc], 1u << lc, g.smem_cl[lc], ctx->d_err.p,
                                st, t0, t1));
     }
     for (int j = 1; j < k; ++j) {   // join
@@ -1203,6 +1204,7 @@ static int run_good_only(rtlfs_ctx *ctx) {
     CU(cudaMemcpyAsync(&err, ctx->d_err.p, sizeof(err), cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
     if (err & 1u) return fail(ctx, RTLFS_E_CUDA, "good-trace staging did not complete (bounded wait ran out)");
+    if (err & 4u) return fail(ctx, RTLFS_E_CUDA, "a cluster good-trace launch did not run in its clusters");
     for (Design *D : ctx->designs) D->trace_valid = true;
     return RTLFS_OK;
 }
@@ -1623,6 +1625,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
             return fail(ctx, RTLFS_E_NOMEM, "heavy register-diff pool overflowed; run with window = 0");
         if (kerr & 1u)
             return fail(ctx, RTLFS_E_CUDA, "good-trace staging did not complete (bounded wait ran out)");
+        if (kerr & 4u)
+            return fail(ctx, RTLFS_E_CUDA, "a cluster good-trace launch did not run in its clusters");
     }
     const unsigned long long *heads = ctx->p_small;
     const uint32_t *cnts = reinterpret_cast<const uint32_t *>(ctx->p_small + 8);
@@ -1760,6 +1764,7 @@ int rtlfs_run_plain(rtlfs_ctx *ctx, rtlfs_result *const *out) {
     CU(cudaEventRecord(ev[5], ctx->s_main));
     CU(cudaStreamSynchronize(ctx->s_main));
     if (gerr & 1u) return fail(ctx, RTLFS_E_CUDA, "good-trace staging did not complete (bounded wait ran out)");
+    if (gerr & 4u) return fail(ctx, RTLFS_E_CUDA, "a cluster good-trace launch did not run in its clusters");
     for (Design *D : ctx->designs) D->trace_valid = true;
     rtlfs_stats &st = ctx->stats;
     st = rtlfs_stats{};

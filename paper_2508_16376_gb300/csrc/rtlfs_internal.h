@@ -245,8 +245,9 @@ size_t good_cluster_smem_bytes(uint32_t own, uint32_t rown, uint32_t n_inputs, u
 // Clusters of C CTAs with `smem` bytes each that can be resident at once (0: none).
 int good_cluster_max_active(uint32_t C, size_t smem);
 // Good trace of the listed designs over cycles [t_begin, t_end), one cluster of C CTAs each.
+// A launch that does not run in clusters of C CTAs does nothing and sets bit 2 of *err.
 cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *design_list,
-                                uint32_t n_list, uint32_t C, size_t smem,
+                                uint32_t n_list, uint32_t C, size_t smem, uint32_t *err,
                                 cudaStream_t stream, uint32_t t_begin, uint32_t t_end);
 cudaError_t launch_light(const DevDesign *d_designs, DevFaults f, Queues q, int cap, int block,
                          int grid, cudaStream_t stream);

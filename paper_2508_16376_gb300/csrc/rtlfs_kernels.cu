@@ -395,9 +395,16 @@ __device__ __forceinline__ uint64_t dsm_load(uint32_t local_addr, uint32_t rank)
 
 __global__ void __launch_bounds__(GOOD_BLOCK, 1)
 good_cluster_kernel(const DevDesign *__restrict__ designs, const uint32_t *__restrict__ list,
-                    uint32_t t_begin, uint32_t t_end) {
+                    uint32_t C_launch, uint32_t *err, uint32_t t_begin, uint32_t t_end) {
     extern __shared__ __align__(128) uint64_t gsm[];
     const uint32_t rank = cluster_rank(), C = cluster_ctas();
+    // The design list and every CTA's share assume clusters of C_launch CTAs: a launch that
+    // did not get them (a tool replaying it without the cluster attribute) returns at once,
+    // in every CTA before any cluster barrier, and flags the error.
+    if (C != C_launch) {
+        if (threadIdx.x == 0) atomicOr(err, 4u);
+        return;
+    }
     const DevDesign &D = designs[list[blockIdx.x / C]];
     const uint32_t I = D.I, IR = I + D.R, n_net = D.n_net;
     const uint32_t T = min(D.T, t_end);
@@ -655,6 +662,11 @@ __device__ __forceinline__ void heavy_zero(const HeavySmem &m, const HeavyScratc
 
 // Loads issued where they stand: volatile, so the compiler does not sink them into the
 // branch that consumes them and they travel together with the operand loads.
+// Ask L2 for the line holding p (no register result, no fault on a valid address).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ uint32_t ld_early_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -1032,6 +1044,13 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
     };
     auto mark = [&](uint32_t c, uint32_t lv) {
         const uint32_t b1 = 1u << (c & 31u);
+#ifdef RTLFS_HEAVY_PREFETCH
+        // node c is evaluated at a later level of this cycle: start its descriptor, net
+        // record and good value on their way to L2 now
+        prefetch_l2(D.desc + c);
+        prefetch_l2(netinfo + IR + c);
+        prefetch_l2(gcol + (size_t)(IR + c) * T + t);
+#endif
         if (GBM) {
             // a reduction on the global word (no value back) and its summary bit; the level's
             // count may include a node marked twice, which only errs towards the scan path
@@ -1581,6 +1600,11 @@ __device__ __forceinline__ void light_run_fault(const DevDesign &D, const DevFau
 
         auto heap_push = [&](uint32_t x) {
             if (nh >= (uint32_t)KH) { ovf = true; return; }
+#ifdef RTLFS_HEAVY_PREFETCH
+            prefetch_l2(desc + x);
+            prefetch_l2(netinfo + IR + x);
+            prefetch_l2(gcol + (size_t)(IR + x) * T + t);
+#endif
             uint32_t i = nh++;
             while (i > 0) {
                 const uint32_t p = (i - 1) >> 1;
@@ -2035,7 +2059,7 @@ int good_cluster_max_active(uint32_t C, size_t smem) {
 }
 
 cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *design_list,
-                                uint32_t n_list, uint32_t C, size_t smem,
+                                uint32_t n_list, uint32_t C, size_t smem, uint32_t *err,
                                 cudaStream_t stream, uint32_t t_begin, uint32_t t_end) {
     if (n_list == 0) return cudaSuccess;
     cudaError_t e = good_cluster_attrs(C, smem);
@@ -2052,7 +2076,7 @@ cudaError_t launch_good_cluster(const DevDesign *d_designs, const uint32_t *desi
     cfg.stream = stream;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, good_cluster_kernel, d_designs, design_list, t_begin, t_end);
+    return cudaLaunchKernelEx(&cfg, good_cluster_kernel, d_designs, design_list, C, err, t_begin, t_end);
 }
 
 cudaError_t launch_transpose(uint64_t *gcol, const uint64_t *rows, uint32_t n_net, uint32_t T,

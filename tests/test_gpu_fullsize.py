@@ -1,12 +1,15 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py times (its own
 workload and options, imported from it), for each fault list and mode it can time.
 
-The oracle cannot finish 100k faults x 10k cycles of the medium design in a test, so it
-checks a stratified sample fault by fault -- the highest propagation loads, the latest
-detections, faults on FSM state bits and a uniform remainder -- and the plain GPU form
-(an independent kernel) checks every fault. The large design runs a subsample of its
-faults over all 20k cycles. The load predictor's effect is measured on the medium
-campaign: identical results, and whether its ranking of fault loads beats the heuristic's.
+Every fault is compared with the plain GPU form (one thread per fault, its own kernel and
+its own per-thread state). The plain form is not independent of the path under test: it
+shares the host's design build (levelizing, renumbering, fan-out and latch maps), the op
+evaluator and the good trace, so a mistake there would pass this comparison. What pins the
+results to the problem's definition is the oracle: here a stratified sample fault by fault
+(the highest propagation loads, the latest detections, faults on FSM state bits and a
+uniform remainder), and the stored whole-list oracle results in tests/test_gpu_golden.py.
+The load predictor's effect is measured on the medium campaign: identical results, and
+whether its ranking of fault loads beats the heuristic's.
 """
 import os
 
@@ -44,12 +47,13 @@ def _stratified(res, loads, faults, design, k, seed):
 
 
 def test_medium_full_size():
-    """The bench workload (20k nodes, 10k cycles, 100k faults) in the launch configuration
-    the bench times (windows of 256 cycles, light capacity 1) and in the one-pass form."""
+    """The bench's medium workload (20k nodes, 10k cycles, 100k faults) in the launch
+    configuration the bench times it with and in the one-pass form."""
     d, stim, f = bench.workload(0)
     with Simulator(0) as sim:
         sim.add(d, stim, f)
-        res, loads = sim.run(want_load=True, **bench.DEFAULT_OPTS)
+        opts, _ = bench.campaign_options(sim, "medium")
+        res, loads = sim.run(want_load=True, **opts)
         res1, loads1 = sim.run(want_load=True)
         plain = sim.run_plain()
     for a, b, c in zip(split(res[0]), split(plain[0]), split(res1[0])):
@@ -69,7 +73,8 @@ def test_medium_full_size_fault_models(model):
     d, stim, f = bench.workload(0, 0, model)
     with Simulator(0) as sim:
         sim.add(d, stim, f)
-        res, loads = sim.run(want_load=True, **bench.DEFAULT_OPTS)
+        opts, _ = bench.campaign_options(sim, "medium")
+        res, loads = sim.run(want_load=True, **opts)
         plain = sim.run_plain()
     for a, b in zip(split(res[0]), split(plain[0])):
         assert np.array_equal(a, b)
@@ -112,15 +117,17 @@ def test_medium_full_size_checkpoint():
 
 
 def test_large_design_subsample():
-    """200k nodes, 20k registers, 256/256 ports, 8 FSMs, all 20k cycles; 20k of the
-    sampled faults; a stratified handful against the oracle (each takes seconds)."""
+    """200k nodes, 20k registers, 256/256 ports, 8 FSMs, all 20k cycles; 3000 of the
+    sampled faults (one wave of the plain form) in the large campaign's benchmark options,
+    every one against the plain GPU form; a stratified handful against the oracle."""
     d = synth.large_design(4)
     stim = synth.stimulus(d, 20000, 104)
-    f = synth.sample_faults(d, 20000, 204)
+    f = synth.sample_faults(d, 3000, 204)
     with Simulator(0) as sim:
         sim.add(d, stim, f)
-        res, loads = sim.run(want_load=True, heavy_frac=0.02)
-        res2, _ = sim.run(scheduler=rtlfs.SCHED_PLAIN)
+        opts, _ = bench.campaign_options(sim, "large")
+        res, loads = sim.run(want_load=True, **opts)
+        res2 = sim.run_plain()
     for a, b in zip(split(res[0]), split(res2[0])):
         assert np.array_equal(a, b)
     idx = _stratified(res[0], loads[0], f, d, 3, 2)
