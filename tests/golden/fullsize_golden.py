@@ -16,6 +16,7 @@ The strata are structural (read from the design's arrays), never taken from a GP
 
   python tests/golden/fullsize_golden.py {medium,large,batch} [--part K[-L]/N] [--threads T]
                                           [--deadline SECONDS] [--out DIR]
+                                          [--uniform N] [--fanout M] [--draw D]
 
 A part K/N takes every N-th selected fault starting at K (a uniform sample of the
 selection; K-L/N takes parts K..L); with a deadline the script stops taking new faults when it expires and stores
@@ -88,17 +89,19 @@ def fingerprint(d, stim, faults) -> str:
     return h.hexdigest()
 
 
-def cases(name: str):
-    """[(design index, design, stimulus, faults, selected fault indices)] for a workload."""
+def cases(name: str, pick=None, seed_offset: int = 0):
+    """[(design index, design, stimulus, faults, selected fault indices)] for a workload;
+    `pick` = (uniform, widest fan-out) overrides the subsample sizes and `seed_offset` draws
+    another uniform remainder (results already stored for other draws stay valid)."""
     from paper_2508_16376_gb300 import synth
     if name == "medium":
         d, stim, f = synth.workload("medium")
         return [(0, d, stim, f, np.arange(len(f)))]
     if name == "large":
         d, stim, f = synth.workload("large")
-        return [(0, d, stim, f, stratified(d, f, *LARGE_PICK, seed=41))]
+        return [(0, d, stim, f, stratified(d, f, *(pick or LARGE_PICK), seed=41 + seed_offset))]
     if name == "batch":
-        return [(i, d, stim, f, stratified(d, f, *BATCH_PICK, seed=4100 + i))
+        return [(i, d, stim, f, stratified(d, f, *(pick or BATCH_PICK), seed=4100 + i + 1000 * seed_offset))
                 for i, (d, stim, f) in enumerate(synth.batch_workload())]
     raise ValueError(name)
 
@@ -131,6 +134,9 @@ def main() -> int:
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--deadline", type=float, default=0.0, help="seconds; 0 = none")
     ap.add_argument("--out", default=DIR)
+    ap.add_argument("--uniform", type=int, default=0, help="uniform faults per design (0: default)")
+    ap.add_argument("--fanout", type=int, default=-1, help="widest-fan-out faults per design (-1: default)")
+    ap.add_argument("--draw", type=int, default=0, help="another uniform draw (its seed offset)")
     args = ap.parse_args()
     import oracle
     oracle.build()
@@ -142,7 +148,11 @@ def main() -> int:
     todo = []   # (design index, fault indices of one chunk)
     ctx = {}
     stored = load(args.name)   # faults already stored under tests/golden/fullsize are skipped
-    for di, d, stim, f, sel in cases(args.name):
+    default = LARGE_PICK if args.name == "large" else BATCH_PICK
+    pick = None
+    if args.uniform or args.fanout >= 0:
+        pick = (args.uniform or default[0], args.fanout if args.fanout >= 0 else default[1])
+    for di, d, stim, f, sel in cases(args.name, pick, args.draw):
         mine = np.sort(np.concatenate([sel[k::n] for k in parts]))
         if di in stored:   # faults an earlier run already stored
             mine = mine[~np.isin(mine, stored[di][1])]
