@@ -514,8 +514,10 @@ def main():
             "clocks": clk.summary()}
     ints = roofline.int_peak(peaks, line["clocks"].get("sm_mhz"),
                              torch.cuda.get_device_properties(local).multi_processor_count)
+    traffic = (roofline.heavy_traffic_per_launch(last, n_win, last.get("heavy_form") == 3)
+               if roofline.dominant(mean)[0] == "heavy" else None)
     line["roofline"] = roofline.step_roofline(my_parts, my_results, last, mean, run_opts,
-                                              peaks, n_win, dev_ms, ints)
+                                              peaks, n_win, dev_ms, ints, traffic=traffic)
     line["roofline_alu"] = roofline.step_alu(my_parts, last, mean, n_win, dev_ms, ints)
 
     if rank == 0 and args.checkpoint_at:

@@ -200,7 +200,8 @@ typedef struct {
     uint64_t promoted;       /* light faults promoted to the heavy kernel */
     uint64_t heavy_initial;  /* faults assigned to the heavy kernel from cycle 0 */
     uint32_t n_launches;     /* kernels launched by the run */
-    uint32_t reserved;
+    uint32_t heavy_form;     /* heavy kernel's record of differing nets in the run: 1 exact,
+                                2 stamped, 3 stamped with the node bitmap in global scratch */
     uint64_t light_evals;         /* node evaluations done by the light kernel */
     uint64_t light_fault_cycles;  /* fault-cycles completed by the light kernel */
     uint64_t heavy_evals;         /* node evaluations done by the heavy kernel */

@@ -1678,6 +1678,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         st.promoted = cnts[0] - st.heavy_initial;
     }
     st.n_launches = launches;
+    st.heavy_form = ctx->heavy_gbm ? 3u : ctx->heavy_exact ? 1u : 2u;
     st.light_evals = heads[4];
     st.light_fault_cycles = heads[5];
     st.heavy_evals = heads[6];

@@ -662,11 +662,6 @@ __device__ __forceinline__ void heavy_zero(const HeavySmem &m, const HeavyScratc
 
 // Loads issued where they stand: volatile, so the compiler does not sink them into the
 // branch that consumes them and they travel together with the operand loads.
-// Ask L2 for the line holding p (no register result, no fault on a valid address).
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ uint32_t ld_early_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -1044,13 +1039,6 @@ __device__ __forceinline__ void heavy_run_fault_warp(const DevDesign &D, const D
     };
     auto mark = [&](uint32_t c, uint32_t lv) {
         const uint32_t b1 = 1u << (c & 31u);
-#ifdef RTLFS_HEAVY_PREFETCH
-        // node c is evaluated at a later level of this cycle: start its descriptor, net
-        // record and good value on their way to L2 now
-        prefetch_l2(D.desc + c);
-        prefetch_l2(netinfo + IR + c);
-        prefetch_l2(gcol + (size_t)(IR + c) * T + t);
-#endif
         if (GBM) {
             // a reduction on the global word (no value back) and its summary bit; the level's
             // count may include a node marked twice, which only errs towards the scan path
@@ -1600,11 +1588,6 @@ __device__ __forceinline__ void light_run_fault(const DevDesign &D, const DevFau
 
         auto heap_push = [&](uint32_t x) {
             if (nh >= (uint32_t)KH) { ovf = true; return; }
-#ifdef RTLFS_HEAVY_PREFETCH
-            prefetch_l2(desc + x);
-            prefetch_l2(netinfo + IR + x);
-            prefetch_l2(gcol + (size_t)(IR + x) * T + t);
-#endif
             uint32_t i = nh++;
             while (i > 0) {
                 const uint32_t p = (i - 1) >> 1;

@@ -54,7 +54,7 @@ class rtlfs_stats(ctypes.Structure):
                 ("light_ms", ctypes.c_double), ("heavy_ms", ctypes.c_double),
                 ("fault_cycles", ctypes.c_uint64), ("node_evals", ctypes.c_uint64),
                 ("promoted", ctypes.c_uint64), ("heavy_initial", ctypes.c_uint64),
-                ("n_launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_launches", ctypes.c_uint32), ("heavy_form", ctypes.c_uint32),
                 ("light_evals", ctypes.c_uint64), ("light_fault_cycles", ctypes.c_uint64),
                 ("heavy_evals", ctypes.c_uint64), ("heavy_fault_cycles", ctypes.c_uint64)]
 
