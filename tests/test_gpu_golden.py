@@ -45,7 +45,7 @@ def _check(name, parts, results, offset=0):
     assert stored, f"no stored oracle results for {name}"
     n = 0
     for di, (fp, idx, det, cyc, port) in stored.items():
-        d, stim, f = parts[di]
+        d, stim, f = parts[offset + di]
         assert golden.fingerprint(d, stim, f) == fp, f"{name} design {di}: inputs differ from the stored ones"
         gdet, gcyc, gport = (np.asarray(x)[idx] for x in split(results[offset + di]))
         bad = np.nonzero((gdet != det) | (gcyc != cyc) | (gport != port))[0]
