@@ -1384,8 +1384,11 @@ heavy_kernel(const DevDesign *__restrict__ designs, DevFaults f, Queues q, Heavy
 // Windowed heavy kernel: the heavy kernel over cycles [t0, t1) for the faults carried
 // from the last window and those promoted in this one; survivors carry their register
 // diffs to the next window through the pool.
+// One-warp CTAs: 24 resident per SM at the 80 registers the exact and stamped forms take;
+// the global-bitmap form (large designs, whose level steps wait on DRAM misses) is held to
+// 64 registers (a few spilled bytes) so that 32 faults are in flight per SM.
 template <bool WARP, bool EXACT, bool GBM = false>
-__global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? 24 : 1)
+__global__ void __launch_bounds__(WARP ? 32 : 1024, WARP ? (GBM ? 32 : 24) : 1)
 heavy_window_kernel(const DevDesign *__restrict__ designs, DevFaults f, WinHeavy q, HeavyScratch S) {
     extern __shared__ __align__(16) uint32_t hsm[];
     __shared__ HeavyVars V;
