@@ -519,6 +519,7 @@ def main():
     line["roofline"] = roofline.step_roofline(my_parts, my_results, last, mean, run_opts,
                                               peaks, n_win, dev_ms, ints, traffic=traffic)
     line["roofline_alu"] = roofline.step_alu(my_parts, last, mean, n_win, dev_ms, ints)
+    line["roofline_bound"] = roofline.step_bound(line["roofline"], line["roofline_alu"], dev_ms)
 
     if rank == 0 and args.checkpoint_at:
         line["checkpoint"] = time_checkpoint(sim, *my_parts[0], run_opts, args.checkpoint_at, local)

@@ -162,6 +162,17 @@ def step_roofline(parts, results, stats: dict, mean_ms: dict, run_opts: dict, pe
             "step_achieved": step, "step_frac": step / peak, "traffic": traffic}
 
 
+def step_bound(hbm: dict, alu: dict, step_ms: float) -> dict:
+    """The step's lower bound max(algorithmic bytes / HBM peak, algorithmic integer ops /
+    integer peak) and its ratio to the measured step time."""
+    t_bytes = hbm["algorithmic_bytes_per_step"] / (hbm["peak"] * 1e9)
+    t_ops = alu["int_ops_per_step"] / (alu["peak"] * 1e12)
+    bound = max(t_bytes, t_ops)
+    return {"bytes_s": t_bytes, "int_ops_s": t_ops, "bound_s": bound,
+            "bound_by": "hbm" if t_bytes >= t_ops else "alu", "measured_s": step_ms / 1000.0,
+            "frac": bound / (step_ms / 1000.0) if step_ms > 0 else 0.0}
+
+
 def step_alu(parts, stats: dict, mean_ms: dict, n_win: int, step_ms: float, ints: dict) -> dict:
     """Integer-ALU roofline: the step's algorithmic 32-bit integer operations over the
     dominant kernel's time and over the whole step, against SMs x lanes x clock."""

@@ -28,7 +28,7 @@ def test_bench_line(config, cycles):
     j = _line("--config", config, "--cycles", str(cycles))
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "clocks",
-              "roofline", "roofline_alu", "plain_gpu_form"):
+              "roofline", "roofline_alu", "roofline_bound", "plain_gpu_form"):
         assert k in j, k
     assert j["metric"] == bench.METRIC and j["unit"] == bench.UNIT and j["steps"] == 2
     assert j["value"] > 0 and j["e2e"]["value"] > 0 and j["e2e"]["h2d_bytes_per_step"] > 0

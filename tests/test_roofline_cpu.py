@@ -55,3 +55,6 @@ def test_fractions_are_achieved_over_peak():
     a = roofline.step_alu(parts, stats, mean, 1, 1.0, ints)
     assert abs(a["frac"] - a["achieved"] / ints["tops"]) < 1e-12
     assert a["int_ops_per_step"] == roofline.step_int_ops(parts, stats)["total"]
+    b = roofline.step_bound(r, a, 2.0)
+    assert b["bound_s"] == max(r["algorithmic_bytes_per_step"] / 1e12, a["int_ops_per_step"] / (ints["tops"] * 1e12))
+    assert abs(b["frac"] - b["bound_s"] / 2e-3) < 1e-12 and b["bound_by"] in ("hbm", "alu")
