@@ -185,6 +185,11 @@ typedef struct {
                                 kernels never wait for the good trace; 0 = the good trace of
                                 window w+1 overlaps the faulty kernels of window w. Ignored
                                 by a run that stops at stop_cycle or resumes. Same results */
+    int32_t  order_classes;  /* HEURISTIC / MLP schedule: 0 = the queue in descending score
+                                order (4096 score buckets); 1, 2, 4, .. 64 = that many score
+                                classes, highest first, each keeping the fault-list order (a
+                                warp's light lanes then take faults of neighbouring sites);
+                                RTLFS_E_ARG otherwise. Same results */
 } rtlfs_run_opts;
 
 /* Timing and counters of the last rtlfs_run (milliseconds from CUDA events). */

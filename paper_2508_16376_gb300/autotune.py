@@ -2,8 +2,10 @@
 and heavy kernels; 0 = one pass over all cycles), the light-lane capacity, the fraction of
 faults the scheduler sends to the heavy kernel from cycle 0 (the light/heavy split), and
 the CTA sizes of the light kernel (lanes per CTA) and of the heavy kernel (threads per
-heavy fault), and whether the whole good trace runs before the first faulty window
-(good_first) or window by window, overlapped with the faulty kernels.
+heavy fault), whether the whole good trace runs before the first faulty window
+(good_first) or window by window, overlapped with the faulty kernels, and how coarsely the
+scheduler orders the queue (order_classes: fine score order, or a few score classes each
+kept in fault-list order).
 
 Every candidate is timed with real campaigns through rtlfs_run on the workload loaded in
 the simulator (device-event time of the whole campaign, best of `repeats`). The search is
@@ -24,7 +26,8 @@ from .rtlfs import SCHED_HEURISTIC, SCHED_MLP
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 
-BASE = dict(window=256, light_cap=1, heavy_frac=0.0, light_block=128, heavy_block=32, good_first=0)
+BASE = dict(window=256, light_cap=1, heavy_frac=0.0, light_block=128, heavy_block=32, good_first=0,
+            order_classes=0)
 KNOBS: List[Tuple[str, Sequence]] = [
     ("window", (256, 128, 512, 64, 0)),
     ("light_cap", (1, 2)),
@@ -32,6 +35,7 @@ KNOBS: List[Tuple[str, Sequence]] = [
     ("light_block", (128, 64, 256)),
     ("heavy_block", (32, 64)),
     ("good_first", (0, 1)),
+    ("order_classes", (0, 8, 1)),
 ]
 
 

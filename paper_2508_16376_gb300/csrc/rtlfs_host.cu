@@ -1231,6 +1231,8 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
     ctx->good_cluster = (uint32_t)o.good_cluster;
     if (o.good_staging < 0 || o.good_staging > 1) return fail(ctx, RTLFS_E_ARG, "good_staging must be 0 or 1");
     if (o.good_first < 0 || o.good_first > 1) return fail(ctx, RTLFS_E_ARG, "good_first must be 0 or 1");
+    if (o.order_classes < 0 || o.order_classes > 64 || (o.order_classes & (o.order_classes - 1)))
+        return fail(ctx, RTLFS_E_ARG, "order_classes must be 0 or a power of two up to 64");
     ctx->good_staging = (uint32_t)o.good_staging;
     CU(cudaSetDevice(ctx->device));
     const auto t_host0 = std::chrono::steady_clock::now();
@@ -1435,7 +1437,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                         ++launches;
                     }
                     CU(launch_order(score, F, ctx->d_mm.p, ctx->d_hist.p, ctx->d_order.p, n_heavy,
-                                    ctx->d_prom_items.p, ctx->s_main));
+                                    ctx->d_prom_items.p, ctx->s_main, (uint32_t)o.order_classes));
                     launches += 6 + (n_heavy ? 1 : 0);
                 }
                 CU(cudaEventRecord(ev[6], ctx->s_main));
@@ -1540,7 +1542,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
                 ++launches;
             }
             CU(launch_order(score, F, ctx->d_mm.p, ctx->d_hist.p, ctx->d_order.p, n_heavy,
-                            ctx->d_init_items.p, ctx->s_main));
+                            ctx->d_init_items.p, ctx->s_main, (uint32_t)o.order_classes));
             launches += 6 + (n_heavy ? 1 : 0);
         }
         CU(cudaEventRecord(ev[6], ctx->s_main));
@@ -1572,7 +1574,7 @@ int rtlfs_run(rtlfs_ctx *ctx, const rtlfs_run_opts *opts_in, rtlfs_result *const
         std::vector<uint64_t> key = {F, n_heavy, ql.n_light, (uint64_t)lcap, (uint64_t)lblock,
                                      (uint64_t)lgrid, (uint64_t)hblock, (uint64_t)hgrid,
                                      (uint64_t)dev_sched, (uint64_t)use_mlp, o.fault_budget, W,
-                                     (uint64_t)nodrop, (uint64_t)good_first};
+                                     (uint64_t)nodrop, (uint64_t)good_first, (uint64_t)o.order_classes};
         const void *ptrs[] = {ctx->d_designs.p, ctx->d_list_smem.p, ctx->d_list_glob.p, ctx->d_order.p, ctx->d_err.p, ctx->h_gbm.p,
                               ctx->d_init_items.p, ctx->d_prom_items.p, ctx->d_heads.p, ctx->d_counters.p,
                               ctx->d_load.p, ctx->d_cycle.p, ctx->d_port.p, ctx->d_det.p, ctx->d_site.p,

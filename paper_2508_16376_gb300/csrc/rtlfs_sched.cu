@@ -210,12 +210,23 @@ __global__ void mlp_adam_kernel(float *master, __nv_bfloat16 *wb, float *grad, f
 }
 
 // ---- queue order -----------------------------------------------------------------------
-// Counting sort of the faults by score, descending, into NB buckets over [lo, hi].
-__device__ __forceinline__ uint32_t bucket_of(float s, float lo, float hi) {
+// Counting sort of the faults by score, descending, into SORT_BUCKETS buckets over [lo, hi].
+// With k > 0 score classes (a power of two up to 64) the buckets are k classes of
+// SORT_BUCKETS / k sub-buckets each: fault i of n goes to its class's sub-bucket
+// i * (SORT_BUCKETS / k) / n, so inside a class the queue keeps the fault-list order (by
+// site), at the granularity of a sub-bucket. Every bucket index is below SORT_BUCKETS.
+__device__ __forceinline__ uint32_t bucket_of(float s, float lo, float hi, uint32_t i, uint32_t n,
+                                              uint32_t k) {
     float u = hi > lo ? (s - lo) / (hi - lo) : 0.f;
     u = fminf(fmaxf(u, 0.f), 1.f);
-    const uint32_t b = (uint32_t)(u * (float)(SORT_BUCKETS - 1) + 0.5f);
-    return (SORT_BUCKETS - 1) - b;    // descending score = ascending bucket
+    if (k == 0) {
+        const uint32_t b = (uint32_t)(u * (float)(SORT_BUCKETS - 1) + 0.5f);
+        return (SORT_BUCKETS - 1) - b;    // descending score = ascending bucket
+    }
+    const uint32_t per = SORT_BUCKETS / k;
+    const uint32_t c = min((uint32_t)(u * (float)k), k - 1u);
+    const uint32_t sb = min((uint32_t)(((uint64_t)i * per) / max(n, 1u)), per - 1u);
+    return (k - 1u - c) * per + sb;
 }
 
 __device__ __forceinline__ int map_key(float f) {
@@ -249,14 +260,15 @@ __global__ void minmax_kernel(const float *score, uint32_t n, float *mm) {
     }
 }
 
-__global__ void histogram_kernel(const float *score, uint32_t n, const float *mm, uint32_t *hist) {
+__global__ void histogram_kernel(const float *score, uint32_t n, const float *mm, uint32_t *hist,
+                                 uint32_t k) {
     __shared__ uint32_t h[SORT_BUCKETS];
     for (uint32_t b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const float lo = unmap_key(reinterpret_cast<const int *>(mm)[0]);
     const float hi = unmap_key(reinterpret_cast<const int *>(mm)[1]);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(&h[bucket_of(score[i], lo, hi)], 1u);
+        atomicAdd(&h[bucket_of(score[i], lo, hi, i, n, k)], 1u);
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x)
         if (h[b]) atomicAdd(&hist[b], h[b]);
@@ -284,11 +296,11 @@ __global__ void scan_kernel(uint32_t *hist) {
 // Scatter fault ids into their buckets (order inside a bucket is unspecified), then the
 // first n_heavy go to the heavy kernel's initial list and the rest form the light queue.
 __global__ void scatter_kernel(const float *score, uint32_t n, const float *mm, uint32_t *cursor,
-                               uint32_t *order) {
+                               uint32_t *order, uint32_t k) {
     const float lo = unmap_key(reinterpret_cast<const int *>(mm)[0]);
     const float hi = unmap_key(reinterpret_cast<const int *>(mm)[1]);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t p = atomicAdd(&cursor[bucket_of(score[i], lo, hi)], 1u);
+        const uint32_t p = atomicAdd(&cursor[bucket_of(score[i], lo, hi, i, n, k)], 1u);
         order[p] = i;
     }
 }
@@ -342,16 +354,17 @@ cudaError_t launch_mlp_adam(float *master, void *wb, float *grad, float *m, floa
 }
 
 cudaError_t launch_order(const float *score, uint32_t n, float *mm, uint32_t *hist, uint32_t *order,
-                         uint32_t n_heavy, HeavyItem *items, cudaStream_t s) {
+                         uint32_t n_heavy, HeavyItem *items, cudaStream_t s, uint32_t classes) {
     if (!n) return cudaSuccess;
+    if (classes > 64 || (classes & (classes - 1))) return cudaErrorInvalidValue;
     minmax_init_kernel<<<1, 1, 0, s>>>(mm);
     cudaError_t e = cudaMemsetAsync(hist, 0, SORT_BUCKETS * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const uint32_t g = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
     minmax_kernel<<<g, 256, 0, s>>>(score, n, mm);
-    histogram_kernel<<<g, 256, 0, s>>>(score, n, mm, hist);
+    histogram_kernel<<<g, 256, 0, s>>>(score, n, mm, hist, classes);
     scan_kernel<<<1, 1024, 0, s>>>(hist);
-    scatter_kernel<<<g, 256, 0, s>>>(score, n, mm, hist, order);
+    scatter_kernel<<<g, 256, 0, s>>>(score, n, mm, hist, order, classes);
     if (n_heavy) heavy_items_kernel<<<(n_heavy + 255) / 256, 256, 0, s>>>(order, n_heavy, items);
     return cudaGetLastError();
 }

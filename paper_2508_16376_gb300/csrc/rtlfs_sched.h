@@ -27,8 +27,10 @@ cudaError_t launch_mlp_grad(const void *wb, const float *X, const float *t, uint
 cudaError_t launch_mlp_adam(float *master, void *wb, float *grad, float *m, float *v, float lr,
                             float beta1, float beta2, float eps, int step, cudaStream_t s);
 // Orders the n faults by descending score into order[]; the first n_heavy become heavy
-// items. mm: 2 floats of scratch, hist: SORT_BUCKETS uint32 of scratch.
+// items. mm: 2 floats of scratch, hist: SORT_BUCKETS uint32 of scratch. classes = 0: the
+// fine order (SORT_BUCKETS score buckets); a power of two up to 64: that many score classes,
+// fault-list order kept inside each (cudaErrorInvalidValue otherwise).
 cudaError_t launch_order(const float *score, uint32_t n, float *mm, uint32_t *hist, uint32_t *order,
-                         uint32_t n_heavy, HeavyItem *items, cudaStream_t s);
+                         uint32_t n_heavy, HeavyItem *items, cudaStream_t s, uint32_t classes = 0);
 
 }  // namespace rtlfs

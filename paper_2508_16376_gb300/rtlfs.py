@@ -45,7 +45,8 @@ class rtlfs_run_opts(ctypes.Structure):
                 ("window", ctypes.c_int32), ("no_drop", ctypes.c_int32),
                 ("stop_cycle", ctypes.c_int32), ("resume", ctypes.c_int32),
                 ("heavy_form", ctypes.c_int32), ("good_cluster", ctypes.c_int32),
-                ("good_staging", ctypes.c_int32), ("good_first", ctypes.c_int32)]
+                ("good_staging", ctypes.c_int32), ("good_first", ctypes.c_int32),
+                ("order_classes", ctypes.c_int32)]
 
 
 class rtlfs_stats(ctypes.Structure):

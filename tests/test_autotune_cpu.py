@@ -36,7 +36,7 @@ def separable(best):
 
 def test_knobs_cover_window_split_and_cta_sizes():
     names = dict(autotune.KNOBS)
-    assert set(names) == {"window", "light_cap", "heavy_frac", "light_block", "heavy_block", "good_first"}
+    assert set(names) == {"window", "light_cap", "heavy_frac", "light_block", "heavy_block", "good_first", "order_classes"}
     assert {64, 128, 256, 512, 0} <= set(names["window"])
     assert len(names["light_block"]) >= 3 and len(names["heavy_block"]) >= 2
     for k, vals in autotune.KNOBS:
@@ -45,7 +45,7 @@ def test_knobs_cover_window_split_and_cta_sizes():
 
 def test_coordinate_descent_finds_separable_optimum(tmp_path):
     cache = str(tmp_path / "cache.json")
-    target = dict(window=128, light_cap=2, heavy_frac=0.05, light_block=64, heavy_block=64, good_first=1)
+    target = dict(window=128, light_cap=2, heavy_frac=0.05, light_block=64, heavy_block=64, good_first=1, order_classes=8)
     sim = FakeSim(separable(target))
     best = autotune.tune(sim, cache_path=cache)
     assert {k: best[k] for k in target} == target

@@ -1,5 +1,7 @@
 """GPU tests of the sharded campaign driver and the autotuner on small batches: both must
 give the oracle's results exactly (neither may change a result, only the time)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -84,3 +86,22 @@ def test_good_first_keeps_results(window):
             res, _ = sim.run(window=window, light_cap=1, good_first=1, use_graph=g, heavy_frac=hf)
             for r, e in zip(res, exp):
                 assert np.array_equal(np.stack(split(r)).astype(np.int64), e), (window, g)
+
+
+@pytest.mark.parametrize("classes", [1, 8, 64])
+def test_order_classes_keep_results(classes):
+    """The queue ordered by a few score classes, fault-list order kept inside each (with the
+    predictor and the heuristic score): the oracle's results."""
+    parts = _small_batch()
+    exp = _oracle(parts)
+    with Simulator(0) as sim:
+        for p in parts:
+            sim.add(*p)
+        rtlfs.rtlfs_mlp_set_weights(sim.ctx, np.load(os.path.join(os.path.dirname(os.path.dirname(
+            os.path.abspath(__file__))), "paper_2508_16376_gb300", "predictor_bf16.npy")))
+        for sch, hf in ((rtlfs.SCHED_MLP, 0.0), (rtlfs.SCHED_HEURISTIC, 0.05)):
+            res, _ = sim.run(window=64, light_cap=1, scheduler=sch, heavy_frac=hf, order_classes=classes)
+            for r, e in zip(res, exp):
+                assert np.array_equal(np.stack(split(r)).astype(np.int64), e), (classes, sch)
+        with pytest.raises(rtlfs.RtlfsError):
+            sim.run(window=64, order_classes=3)
