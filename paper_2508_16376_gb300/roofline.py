@@ -42,8 +42,8 @@ from . import synth as _s
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic of the heavy window kernel (global-bitmap form) from one ncu capture of the
-# learned campaign's second window (profiles/heavy_window_learned_ncu_full.md): read + write
-# bytes of that launch and the heavy evaluations it performed. A launch's traffic is taken
+# learned campaign's second window (cycles 256-511 of the large design + 64-design batch,
+# windows of 256): read + write bytes of that launch and the heavy evaluations it performed. A launch's traffic is taken
 # as proportional to its evaluations; valid while the heavy kernel's source is the captured
 # one (the SHA-256 prefix of the text from heavy_run_fault_warp to the light kernel).
 HEAVY_CAPTURE = {"dram_bytes": 207.818438e9 + 25.442838e9, "evals": 966_552_453,
